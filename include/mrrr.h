@@ -1,0 +1,126 @@
+/*
+ * mrrr.h -- C ABI of the GB300 mixed-precision MRRR tridiagonal eigensolver.
+ *
+ * Problem (paper Sec. 1): given a real symmetric tridiagonal T with diagonal
+ * d[0..n-1] and off-diagonal e[0..n-2], compute eigenpairs (lambda_i, z_i),
+ * T z_i = lambda_i z_i, ||z_i||_2 = 1, for an index set
+ * I subset {1..n} with lambda_1 <= ... <= lambda_n.  The method is MRRR
+ * (Algorithm 1) with the mixed-precision scheme of Sec. 3: input/output in
+ * precision x, all sensitive work in a working precision y > x:
+ *
+ *   mrrr_solve_s, MRRR_MIXED : x = binary32, y = binary64  ("single/double")
+ *   mrrr_solve_d, MRRR_MIXED : x = binary64, y = double-double (~106 bits),
+ *                              standing in for the paper's "double/quadruple"
+ *   MRRR_PLAIN               : y = x (the conventional single-precision solver
+ *                              the paper compares against)
+ *
+ * Conventions shared by every entry point:
+ *  - Indices il..iu are 1-based and inclusive.  A value range is the
+ *    half-open interval (vl, vu].
+ *  - d, e, W, Z may be device pointers or host pointers (pageable or
+ *    pinned); host buffers are staged through device memory by the call.
+ *    The caller owns every buffer.  W must hold k entries and Z n x k
+ *    entries, column-major with leading dimension ldz >= n, where
+ *    k = iu - il + 1 (MRRR_INDEX), n (MRRR_ALL) or, for MRRR_VALUE, n
+ *    (the count found is returned in *m_out).
+ *  - W is returned in ascending order and column j of Z belongs to W[j].
+ *    Each column has unit 2-norm and is signed so that an entry of largest
+ *    magnitude is positive.
+ *  - All work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream).  The call returns after the results are complete on that
+ *    stream.  There is no host (CPU) fallback: without a usable CUDA device
+ *    the call fails with MRRR_ERR_CUDA.
+ *  - Return value: 0 on success or a negative mrrr_status code.  On
+ *    MRRR_ERR_NOCONV the outputs are filled but at least one eigenpair did
+ *    not meet its stopping criterion.
+ */
+#ifndef MRRR_H
+#define MRRR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { MRRR_ALL = 0, MRRR_INDEX = 1, MRRR_VALUE = 2 } mrrr_range;
+
+/* MRRR_PLAIN: working precision = I/O precision.  MRRR_MIXED: the next
+ * higher precision (Sec. 3.1). */
+typedef enum { MRRR_PLAIN = 0, MRRR_MIXED = 1 } mrrr_mode;
+
+typedef enum {
+    MRRR_OK = 0,
+    MRRR_ERR_ARG = -1,        /* invalid argument (sizes, ranges, ldz, NULL) */
+    MRRR_ERR_NONFINITE = -2,  /* NaN or Inf in d or e */
+    MRRR_ERR_NOCONV = -3,     /* an eigenpair missed its stopping test; outputs filled */
+    MRRR_ERR_NOMEM = -4,      /* device allocation failed */
+    MRRR_ERR_CUDA = -5,       /* CUDA runtime error / no device */
+    MRRR_ERR_TIMEOUT = -6,    /* a bounded device-side wait ran out */
+    MRRR_ERR_NOREP = -7       /* informational: no candidate passed the representation test */
+} mrrr_status;
+
+/* Per-solve statistics (optional output). */
+typedef struct {
+    int nblocks;          /* blocks after splitting (Sec. 3.2, Preprocessing) */
+    int d_max;            /* depth of the representation tree (Sec. 2) */
+    int nclusters;        /* clusters processed (Algorithm 1, lines 14-17) */
+    int largest_cluster;  /* size of the largest cluster; rho = largest_cluster / n */
+    int reps_failed;      /* accepted representations that failed the growth test */
+    int rqi_iters;        /* Rayleigh quotient iterations, all eigenpairs */
+    int fallbacks;        /* eigenpairs that needed the bisection fallback */
+    int noconv;           /* eigenpairs that missed the stopping criterion */
+    long long qd_steps_y;   /* qd recurrence steps executed in working precision */
+    long long qd_steps_low; /* qd recurrence steps executed in a lower precision */
+} mrrr_stats;
+
+/* Tuning parameters; a zero field selects the default given in brackets. */
+typedef struct {
+    double gaptol;     /* classification tolerance, Eq. (3.3) [PLAIN 1e-3 (x=d) / 3e-3 (x=s);
+                          MIXED 1e-5 (s/d), 1e-10 (d/dd)] */
+    double xi;         /* bound of the random relative perturbation of the root
+                          representation, Algorithm 1 line 2 [PLAIN 8 eps_x; MIXED 4 eps_x] */
+    double krs;        /* RQI stopping constant k_rs, Eq. (3.5) [1] */
+    int max_depth;     /* depth cap of the representation tree [16] */
+    int max_rqi;       /* RQI steps before the bisection fallback [10] */
+    uint64_t seed;     /* seed of the perturbation sequence [0] */
+    int flags;         /* MRRR_FLAG_* variant bits [0] */
+    mrrr_stats* stats; /* if non-NULL, receives the statistics of the call (host memory) */
+} mrrr_params;
+
+/* Variant bits for mrrr_params.flags. */
+#define MRRR_FLAG_NO_LOWPREC_BISECT 1 /* never pre-bracket eigenvalues in a lower precision */
+#define MRRR_FLAG_IEEE_DIV 2          /* use correctly rounded division in the qd recurrences */
+
+/*
+ * Single-precision input/output (x = binary32).  MRRR_MIXED computes in
+ * binary64 (paper "single/double", Sec. 4.1); MRRR_PLAIN in binary32.
+ * range/vl/vu/il/iu select the eigenpairs as described above.  params may be
+ * NULL (all defaults).  On success *m_out (may be NULL for ALL/INDEX) holds
+ * the number of eigenpairs returned.
+ */
+int mrrr_solve_s(int n, const float* d, const float* e, mrrr_range range, float vl, float vu,
+                 int il, int iu, mrrr_mode mode, const mrrr_params* params, int* m_out,
+                 float* W, float* Z, int ldz, void* stream);
+
+/*
+ * Double-precision input/output (x = binary64).  MRRR_MIXED computes the
+ * representation-tree shifts, the qd transforms and the twisted
+ * factorizations in double-double (the role binary128 plays in the paper's
+ * "double/quadruple" solver, Sec. 4.1); MRRR_PLAIN in binary64.
+ */
+int mrrr_solve_d(int n, const double* d, const double* e, mrrr_range range, double vl, double vu,
+                 int il, int iu, mrrr_mode mode, const mrrr_params* params, int* m_out,
+                 double* W, double* Z, int ldz, void* stream);
+
+/* Human-readable text for a status code (static storage). */
+const char* mrrr_strerror(int status);
+
+/* Library version string (static storage). */
+const char* mrrr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRRR_H */

@@ -1,0 +1,184 @@
+// C ABI (include/mrrr.h): argument checks, host/device staging, parameter
+// defaults, dispatch to the per-precision solvers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "mrrr.h"
+#include "mrrr_entry.h"
+
+namespace {
+
+using mrrr::MatrixDesc;
+using mrrr::SolveCfg;
+
+bool on_device(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Paper defaults (Sec. 2, Sec. 3.2, Sec. 4.1); see mrrr.h.
+SolveCfg make_cfg(bool x_single, bool mixed, const mrrr_params* prm) {
+    SolveCfg c;
+    const double eps_s = 5.9604644775390625e-08, eps_d = 1.1102230246251565e-16, eps_dd = 4.930380657631324e-32;
+    c.eps_x = x_single ? eps_s : eps_d;
+    c.eps_y = mixed ? (x_single ? eps_d : eps_dd) : c.eps_x;
+    c.mixed = mixed ? 1 : 0;
+    double gt = mixed ? (x_single ? 1e-5 : 1e-10) : (x_single ? 3e-3 : 1e-3);
+    double xi = mixed ? 4.0 * c.eps_x : 8.0 * c.eps_x;
+    c.krs = 1.0;
+    c.max_rqi = 10;
+    c.seed = 0;
+    c.flags = 0;
+    if (prm) {
+        if (prm->gaptol > 0) gt = prm->gaptol;
+        if (prm->xi > 0) xi = prm->xi;
+        if (prm->krs > 0) c.krs = prm->krs;
+        if (prm->max_rqi > 0) c.max_rqi = prm->max_rqi;
+        c.seed = prm->seed;
+        c.flags = prm->flags;
+    }
+    c.gaptol = gt;
+    c.rtol_class = 1e-2 * gt;
+    c.xi = xi;
+    c.growth_k = 8.0;
+    return c;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st;
+    explicit DevBuf(cudaStream_t s) : st(s) {}
+    bool alloc(size_t bytes) { return cudaMallocAsync(&p, bytes ? bytes : 1, st) == cudaSuccess; }
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+template <class X>
+int solve_one(int n, const X* d, const X* e, mrrr_range range, X vl, X vu, int il, int iu, mrrr_mode mode,
+              const mrrr_params* prm, int* m_out, X* W, X* Z, int ldz, void* stream) {
+    const bool xs = std::is_same<X, float>::value;
+    if (m_out) *m_out = 0;
+    if (n < 0 || (mode != MRRR_PLAIN && mode != MRRR_MIXED)) return MRRR_ERR_ARG;
+    if (range != MRRR_ALL && range != MRRR_INDEX && range != MRRR_VALUE) return MRRR_ERR_ARG;
+    if (n == 0) return MRRR_OK;
+    if (!d || (n > 1 && !e) || !W || !Z || ldz < n) return MRRR_ERR_ARG;
+    if (range == MRRR_INDEX && (il < 1 || iu > n || il > iu)) return MRRR_ERR_ARG;
+    if (range == MRRR_VALUE && !(vl < vu)) return MRRR_ERR_ARG;
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+        cudaGetLastError();
+        return MRRR_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int kmax = range == MRRR_INDEX ? iu - il + 1 : n;
+    // stage host buffers through device memory
+    DevBuf bd(st), be(st), bw(st), bz(st);
+    const X* dd_ = d;
+    const X* de_ = e;
+    X* dW = W;
+    X* dZ = Z;
+    int dldz = ldz;
+    static const X zero1[1] = {X(0)};
+    if (n == 1) e = zero1;
+    if (!on_device(d)) {
+        if (!bd.alloc(sizeof(X) * n)) return MRRR_ERR_NOMEM;
+        if (cudaMemcpyAsync(bd.p, d, sizeof(X) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) return MRRR_ERR_CUDA;
+        dd_ = (const X*)bd.p;
+    }
+    if (!on_device(e)) {
+        size_t ne = n > 1 ? (size_t)(n - 1) : 1;
+        if (!be.alloc(sizeof(X) * ne)) return MRRR_ERR_NOMEM;
+        if (cudaMemcpyAsync(be.p, e, sizeof(X) * ne, cudaMemcpyHostToDevice, st) != cudaSuccess) return MRRR_ERR_CUDA;
+        de_ = (const X*)be.p;
+    }
+    const bool hostW = !on_device(W), hostZ = !on_device(Z);
+    if (hostW) {
+        if (!bw.alloc(sizeof(X) * kmax)) return MRRR_ERR_NOMEM;
+        dW = (X*)bw.p;
+    }
+    if (hostZ) {
+        if (!bz.alloc(sizeof(X) * (size_t)n * kmax)) return MRRR_ERR_NOMEM;
+        dZ = (X*)bz.p;
+        dldz = n;
+    }
+    MatrixDesc M;
+    memset(&M, 0, sizeof(M));
+    M.d = dd_;
+    M.e = de_;
+    M.W = dW;
+    M.Z = dZ;
+    M.ldz = dldz;
+    M.n = n;
+    M.range = (int)range;
+    M.vl = (double)vl;
+    M.vu = (double)vu;
+    M.il = il;
+    M.iu = iu;
+    SolveCfg cfg = make_cfg(xs, mode == MRRR_MIXED, prm);
+    int max_depth = (prm && prm->max_depth > 0) ? prm->max_depth : 16;
+    mrrr_stats* stats = prm ? prm->stats : nullptr;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    int rc;
+    if (xs) {
+        rc = mode == MRRR_MIXED ? mrrr::solve_batch_s_mixed(1, &M, cfg, max_depth, st, stats)
+                                : mrrr::solve_batch_s_plain(1, &M, cfg, max_depth, st, stats);
+    } else {
+        rc = mode == MRRR_MIXED ? mrrr::solve_batch_d_mixed(1, &M, cfg, max_depth, st, stats)
+                                : mrrr::solve_batch_d_plain(1, &M, cfg, max_depth, st, stats);
+    }
+    if (rc != MRRR_OK && rc != MRRR_ERR_NOCONV) return rc;
+    const int k = M.kout;
+    if (k > 0 && hostW) {
+        if (cudaMemcpyAsync(W, dW, sizeof(X) * k, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MRRR_ERR_CUDA;
+    }
+    if (k > 0 && hostZ) {
+        if (cudaMemcpy2DAsync(Z, sizeof(X) * (size_t)ldz, dZ, sizeof(X) * (size_t)n, sizeof(X) * (size_t)n, k,
+                              cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return MRRR_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MRRR_ERR_CUDA;
+    if (m_out) *m_out = k;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mrrr_solve_s(int n, const float* d, const float* e, mrrr_range range, float vl, float vu, int il, int iu,
+                 mrrr_mode mode, const mrrr_params* params, int* m_out, float* W, float* Z, int ldz, void* stream) {
+    return solve_one<float>(n, d, e, range, vl, vu, il, iu, mode, params, m_out, W, Z, ldz, stream);
+}
+
+int mrrr_solve_d(int n, const double* d, const double* e, mrrr_range range, double vl, double vu, int il, int iu,
+                 mrrr_mode mode, const mrrr_params* params, int* m_out, double* W, double* Z, int ldz,
+                 void* stream) {
+    return solve_one<double>(n, d, e, range, vl, vu, il, iu, mode, params, m_out, W, Z, ldz, stream);
+}
+
+const char* mrrr_strerror(int status) {
+    switch (status) {
+        case MRRR_OK: return "success";
+        case MRRR_ERR_ARG: return "invalid argument";
+        case MRRR_ERR_NONFINITE: return "non-finite value in the input";
+        case MRRR_ERR_NOCONV: return "an eigenpair did not meet its stopping criterion";
+        case MRRR_ERR_NOMEM: return "device memory allocation failed";
+        case MRRR_ERR_CUDA: return "CUDA runtime error or no CUDA device";
+        case MRRR_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+        case MRRR_ERR_NOREP: return "no candidate representation passed the acceptance test";
+        default: return "unknown status";
+    }
+}
+
+const char* mrrr_version(void) { return "mrrr-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,616 @@
+// The steps of Algorithm 1 as per-matrix / per-block / per-item functions.
+// Each CUDA kernel of the solver is a thin wrapper that maps one thread to
+// one call of a function below.
+#pragma once
+
+#include "mrrr_core.cuh"
+#include "mrrr_types.cuh"
+
+#include <type_traits>
+
+#if defined(__CUDA_ARCH__)
+#define MRRR_ATOMIC_ADD(p, v) atomicAdd((p), (v))
+#define MRRR_ATOMIC_MAX(p, v) atomicMax((p), (v))
+#else
+template <class T> static inline T mrrr_host_add(T* p, T v) { T o = *p; *p += v; return o; }
+template <class T> static inline T mrrr_host_max(T* p, T v) { T o = *p; if (v > *p) *p = v; return o; }
+#define MRRR_ATOMIC_ADD(p, v) mrrr_host_add((p), (v))
+#define MRRR_ATOMIC_MAX(p, v) mrrr_host_max((p), (v))
+#endif
+
+namespace mrrr {
+
+template <class X> MRRR_HD double ld_x(const void* p, int i) { return (double)((const X*)p)[i]; }
+
+// --------------------------------------------------------------- a1: scale + split
+
+// Preprocessing (Sec. 2 "Preprocessing", Sec. 3.2 "Preprocessing"): scale T
+// by a power of two so that ||T||_1 lies in [1/2, 1) (exact), set e_i = 0
+// where |e_i| <= eps_x ||T||_1 (||T|| of the unreduced input), and record the
+// irreducible blocks.
+template <class X>
+MRRR_HD void prep_matrix(MatrixDesc& M, BlockDesc* blocks, double* wd, double* we, const SolveCfg& cfg) {
+    const int n = M.n;
+    double tn = 0.0;
+    bool finite = true;
+    for (int i = 0; i < n; ++i) {
+        double di = ld_x<X>(M.d, i);
+        double s = fabs(di);
+        if (!isfinite(di)) finite = false;
+        if (i > 0) s += fabs(ld_x<X>(M.e, i - 1));
+        if (i < n - 1) {
+            double ei = ld_x<X>(M.e, i);
+            if (!isfinite(ei)) finite = false;
+            s += fabs(ei);
+        }
+        tn = fmax(tn, s);
+    }
+    if (!finite || !isfinite(tn)) {
+        M.status = ST_ERR_NONFINITE;
+        M.nblocks = 0;
+        return;
+    }
+    double scale = 1.0;
+    if (tn > 0.0) {
+        int ex;
+        frexp(tn, &ex);  // tn = m 2^ex, m in [1/2, 1)
+        scale = ldexp(1.0, -ex);
+    }
+    M.scale = scale;
+    M.tnorm = tn;
+    const double thresh = cfg.eps_x * tn;
+    int nb = 0;
+    int start = 0;
+    for (int i = 0; i < n; ++i) {
+        wd[M.row0 + i] = ld_x<X>(M.d, i) * scale;
+        bool end = (i == n - 1);
+        if (i < n - 1) {
+            double ei = ld_x<X>(M.e, i);
+            if (fabs(ei) <= thresh) {
+                ei = 0.0;
+                end = true;
+            }
+            we[M.row0 + i] = ei * scale;
+        } else {
+            we[M.row0 + i] = 0.0;
+        }
+        if (end) {
+            BlockDesc& B = blocks[M.row0 + nb];
+            B.matrix = -1;  // set by the caller's matrix index
+            B.row0 = M.row0 + start;
+            B.mrow = start;
+            B.n = i - start + 1;
+            ++nb;
+            start = i + 1;
+        }
+    }
+    M.nblocks = nb;
+}
+
+// --------------------------------------------------------------- a2: root representation
+
+// Root representation (Algorithm 1, lines 1-2): Gershgorin interval, shift
+// mu just outside one end so that T - mu I is definite (Sec. 3.2, the root
+// representation is always found "by making T - mu I definite"), LDL^T in
+// working precision, random relative perturbation, derived LD and LLD.
+// Also decides which local indices the block computes.
+template <class Y>
+MRRR_HD void root_block(BlockDesc& B, const MatrixDesc& M, const double* wd, const double* we, Y* reps,
+                        const SolveCfg& cfg) {
+    const int n = B.n;
+    const double* a = wd + B.row0;
+    const double* b = we + B.row0;
+    Y* rep = reps + 4 * (size_t)B.row0;
+    B.rep_off = 4 * B.row0;
+    double gl = 0.0, gu = 0.0, emax2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double r = 0.0;
+        if (i > 0) r += fabs(b[i - 1]);
+        if (i < n - 1) {
+            r += fabs(b[i]);
+            emax2 = fmax(emax2, b[i] * b[i]);
+        }
+        double lo = a[i] - r, hi = a[i] + r;
+        if (i == 0 || lo < gl) gl = lo;
+        if (i == 0 || hi > gu) gu = hi;
+    }
+    B.pivmin = Prec<Y>::tiny * fmax(1.0, emax2);
+    double bnd = fmax(fabs(gl), fabs(gu));
+    B.spdiam = gu - gl;
+    if (n == 1) {
+        B.mu = a[0];
+        rep[0] = from_d<Y>(0.0);
+        rep[1] = rep[2] = rep[3] = from_d<Y>(0.0);
+        B.gl = 0.0;
+        B.gu = 0.0;
+    } else {
+        // try both ends with a growing safety margin; keep the smaller growth
+        double best = INFINITY;
+        int best_side = 0;
+        double best_mu = 0.0;
+        double delta = 4.0 * n * 1.1102230246251565e-16 * bnd + 4.0 * B.pivmin;
+        for (int attempt = 0; attempt < 40 && !(best < INFINITY); ++attempt) {
+            double muL = gl - delta, muR = gu + delta;
+            double gL = ldl_factor<Y>(a, b, n, muL, +1, rep);
+            double gR = ldl_factor<Y>(a, b, n, muR, -1, rep);
+            if (gL <= gR && gL < INFINITY) {
+                best = gL; best_side = +1; best_mu = muL;
+            } else if (gR < INFINITY) {
+                best = gR; best_side = -1; best_mu = muR;
+            }
+            delta *= 16.0;
+        }
+        if (!(best < INFINITY)) {
+            // cannot happen for finite scaled input; fall back to an indefinite left shift
+            best_mu = gl - delta;
+            best_side = +1;
+        }
+        ldl_factor<Y>(a, b, n, best_mu, best_side, rep);
+        B.mu = best_mu;
+        perturb_and_derive<Y>(rep, n, cfg.xi, cfg.seed, 4ULL * (uint64_t)B.row0);
+        // spectrum of M_root = T - mu I (perturbed by at most ~xi relative): pad the bracket
+        double lo = gl - best_mu, hi = gu - best_mu;
+        double pad = (4.0 * cfg.xi + 8.0 * n * Prec<Y>::eps) * fmax(fabs(lo), fabs(hi)) + 4.0 * B.pivmin;
+        B.gl = lo - pad;
+        B.gu = hi + pad;
+    }
+    // which eigenvalues to compute
+    int wlo = 1, whi = n;
+    if (M.range == RANGE_INDEX && M.nblocks == 1) {
+        wlo = M.il;
+        whi = M.iu;
+    } else if (M.range == RANGE_VALUE) {
+        if (n == 1) {
+            double lam = a[0];
+            bool in = lam > M.vl * M.scale && lam <= M.vu * M.scale;
+            wlo = 1;
+            whi = in ? 1 : 0;
+        } else {
+            Y pm = from_d<Y>(B.pivmin);
+            int cl = negcount<Y>(rep, rep + 3 * n, n, from_d<Y>(M.vl * M.scale - B.mu), pm);
+            int cu = negcount<Y>(rep, rep + 3 * n, n, from_d<Y>(M.vu * M.scale - B.mu), pm);
+            wlo = cl + 1;
+            whi = cu;
+        }
+    }
+    B.w_lo = wlo;
+    B.w_hi = whi;
+    if (wlo > whi) {
+        B.f_lo = 1;
+        B.f_hi = 0;
+    } else {
+        B.f_lo = wlo > 1 ? wlo - 1 : 1;
+        B.f_hi = whi < n ? whi + 1 : n;
+    }
+    B.nitems = B.f_hi >= B.f_lo ? B.f_hi - B.f_lo + 1 : 0;
+}
+
+// Create the items of one block (after the host assigned item0).
+template <class Y>
+MRRR_HD void init_block_items(const BlockDesc& B, int bidx, Item* items, const Y* reps) {
+    for (int t = 0; t < B.nitems; ++t) {
+        Item& I = items[B.item0 + t];
+        I.j = B.f_lo + t;
+        I.lo = B.gl;
+        I.hi = B.gu;
+        I.gapL = INFINITY;
+        I.gapR = INFINITY;
+        I.sig_hi = B.mu;
+        I.sig_lo = 0.0;
+        I.rep = reps + B.rep_off;
+        I.n = B.n;
+        I.block = bidx;
+        I.matrix = B.matrix;
+        I.outcol = -1;
+        I.depth = 0;
+        I.kind = KIND_OPEN;
+        I.wanted = (I.j >= B.w_lo && I.j <= B.w_hi) ? 1 : 0;  // wanted (refined by assign_cols)
+    }
+}
+
+// --------------------------------------------------------------- a3: bisection
+
+template <class T> MRRR_HD T bmax(const T& a, const T& b) { return a < b ? b : a; }
+template <class T> MRRR_HD T bmin(const T& a, const T& b) { return b < a ? b : a; }
+MRRR_HD double babs(double x) { return fabs(x); }
+MRRR_HD dd babs(const dd& x) { return dd_abs(x); }
+MRRR_HD float babs(float x) { return fabsf(x); }
+
+// Bisection for eigenvalue j (1-based) of the rep on the bracket [lo, hi]
+// (Algorithm 1, lines 3 and 16; Sec. 2, "Classification of the
+// eigenvalues"): stop when hi - lo <= max(rtol max(|lo|, |hi|), 2 pivmin).
+// Invariant: negcount(lo) < j <= negcount(hi).  With verify != 0 the
+// invariant is first re-established by widening the bracket (brackets
+// carried over from a parent rep through a shift, whose eigenvalues differ
+// from the parent's by the mixed relative perturbation of the shift).
+// The bracket type Bt is double for classification and the working
+// precision for the bisection fallback of the RQI.  Returns qd steps.
+template <class Y, class Bt>
+MRRR_HD unsigned long long bisect_bracket(const Y* rep, int n, int j, Bt& lo, Bt& hi, double pivmin, double rtol,
+                                          int verify, int max_steps) {
+    const Y* D = rep;
+    const Y* LLD = rep + 3 * n;
+    Y pm = from_d<Y>(pivmin);
+    unsigned long long steps = 0;
+    if (verify) {
+        for (int side = 0; side < 2; ++side) {
+            Bt w = bmax(hi - lo, Bt(4.0 * Prec<double>::eps) * bmax(babs(lo), babs(hi)));
+            w = bmax(w, Bt(4.0 * pivmin));
+            for (int it = 0; it < 200; ++it) {
+                ++steps;
+                if (side == 0) {
+                    if (negcount<Y>(D, LLD, n, Y(lo), pm) < j) break;
+                    lo = lo - w;
+                } else {
+                    if (negcount<Y>(D, LLD, n, Y(hi), pm) >= j) break;
+                    hi = hi + w;
+                }
+                w = w + w;
+            }
+        }
+    }
+    for (int it = 0; it < max_steps; ++it) {
+        Bt width = hi - lo;
+        Bt tol = bmax(Bt(rtol) * bmax(babs(lo), babs(hi)), Bt(2.0 * pivmin));
+        if (!(tol < width)) break;
+        Bt mid = (lo + hi) * Bt(0.5);
+        if (!(lo < mid && mid < hi)) break;
+        ++steps;
+        if (negcount<Y>(D, LLD, n, Y(mid), pm) >= j) hi = mid;
+        else lo = mid;
+    }
+    return steps * (unsigned long long)n;
+}
+
+template <class Y>
+MRRR_HD void bisect_item(Item& I, double pivmin, double rtol, int verify, int max_steps,
+                         unsigned long long* steps_out) {
+    if (I.n == 1) {
+        I.lo = 0.0;
+        I.hi = 0.0;
+        return;
+    }
+    double lo = I.lo, hi = I.hi;
+    unsigned long long s = bisect_bracket<Y, double>((const Y*)I.rep, I.n, I.j, lo, hi, pivmin, rtol, verify, max_steps);
+    I.lo = lo;
+    I.hi = hi;
+    if (steps_out) *steps_out += s;
+}
+
+// --------------------------------------------------------------- output columns
+
+// Output column of item t: position of its eigenvalue among the wanted
+// eigenvalues of its matrix.  One block: j - w_lo.  Several blocks: the rank
+// by (value, block, j), with ties between blocks broken by block order.
+MRRR_HD void assign_col(int t, Item* items, const MatrixDesc* mats, const BlockDesc* blocks) {
+    Item& I = items[t];
+    const MatrixDesc& M = mats[I.matrix];
+    const BlockDesc& B = blocks[I.block];
+    if (M.nblocks == 1) {
+        I.outcol = I.wanted ? I.j - B.w_lo : -1;
+        return;
+    }
+    double key = 0.5 * (I.lo + I.hi) + B.mu;
+    int rank = 0;
+    for (int u = M.item0; u < M.item0 + M.nitems; ++u) {
+        if (u == t) continue;
+        const Item& U = items[u];
+        if (M.range != RANGE_INDEX && !U.wanted) continue;
+        double k2 = 0.5 * (U.lo + U.hi) + blocks[U.block].mu;
+        if (k2 < key || (k2 == key && (U.block < I.block || (U.block == I.block && U.j < I.j)))) ++rank;
+    }
+    if (M.range == RANGE_INDEX) {
+        bool want = (rank + 1 >= M.il) && (rank + 1 <= M.iu);
+        I.wanted = want ? 1 : 0;
+        I.outcol = want ? rank - (M.il - 1) : -1;
+    } else {
+        I.outcol = I.wanted ? rank : -1;
+    }
+}
+
+// --------------------------------------------------------------- a4: classification
+
+MRRR_HD double reldist(const Item& A, const Item& B) {
+    double den = fmax(fmax(fabs(A.lo), fabs(A.hi)), fmax(fabs(B.lo), fabs(B.hi)));
+    double num = B.lo - A.hi;
+    return den > 0.0 ? num / den : INFINITY;
+}
+
+// Partition the items [a, b) that share one rep (Algorithm 1, line 7): j and
+// j+1 are separated when reldist(j, j+1) >= gaptol (Sec. 2, "Classification
+// of the eigenvalues").  Singletons get their gaps and go to the singleton
+// list; clusters with at least one wanted member are appended to the cluster
+// list together with their members.
+MRRR_HD void classify_group(int a, int b, Item* items, double gaptol, int* single_list, Cluster* clusters,
+                            int* member_list, DevCounters* C) {
+    int s = a;
+    while (s < b) {
+        int e = s + 1;
+        while (e < b && reldist(items[e - 1], items[e]) < gaptol) ++e;
+        // run [s, e)
+        double gL = (s > a) ? items[s].lo - items[s - 1].hi : items[s].gapL;
+        double gR = (e < b) ? items[e].lo - items[e - 1].hi : items[e - 1].gapR;
+        if (e - s == 1) {
+            Item& I = items[s];
+            double mid = 0.5 * (I.lo + I.hi);
+            I.gapL = (s > a) ? mid - items[s - 1].hi : I.gapL;
+            I.gapR = (e < b) ? items[e].lo - mid : I.gapR;
+            I.kind = KIND_SINGLETON;
+            if (I.wanted) {
+                int slot = MRRR_ATOMIC_ADD(&C->nsingle, 1);
+                single_list[slot] = s;
+            } else {
+                I.kind = KIND_DROPPED;
+            }
+        } else {
+            int any = 0;
+            for (int u = s; u < e; ++u) any |= items[u].wanted;
+            if (any) {
+                int c = MRRR_ATOMIC_ADD(&C->ncluster, 1);
+                int m0 = MRRR_ATOMIC_ADD(&C->nmember, e - s);
+                unsigned long long off = MRRR_ATOMIC_ADD(&C->pool_need, 4ULL * (unsigned long long)items[s].n);
+                Cluster& K = clusters[c];
+                K.a = s;
+                K.b = e;
+                K.n = items[s].n;
+                K.pool_off = (long long)off;
+                K.gapL = gL;
+                K.gapR = gR;
+                K.depth = items[s].depth;
+                for (int u = s; u < e; ++u) {
+                    items[u].kind = KIND_CLUSTER;
+                    member_list[m0 + (u - s)] = u;
+                }
+                items[s].gapL = gL;
+                items[e - 1].gapR = gR;
+                MRRR_ATOMIC_MAX(&C->largest_cluster, e - s);
+                MRRR_ATOMIC_ADD(&C->nclusters_total, 1);
+            } else {
+                for (int u = s; u < e; ++u) items[u].kind = KIND_DROPPED;
+            }
+        }
+        s = e;
+    }
+}
+
+// --------------------------------------------------------------- a5: cluster -> child rep
+
+// Growth of the child at shift tau as seen by an approximate eigenvector of
+// the cluster: sum_i |d+_i| z_i^2 / ||z||^2, with z the twisted-factorization
+// vector of the parent at tau (tau lies next to the cluster, so z is
+// dominated by the cluster's invariant subspace).  This weighs the element
+// growth by the vector it acts on, as conditional element growth does
+// (Definition "Conditional element growth", Sec. 2): a large pivot where the
+// eigenvector is negligible does no harm.  Uses `work` (3n words).
+template <class Y>
+MRRR_HD double weighted_growth(const Y* parent, int n, Y tau, Y pm, Y* work) {
+    Scratch<Y> Wk;
+    Wk.a = work;
+    Wk.b = work + n;
+    Wk.stride = 1;
+    Y gamma;
+    TwistResult<Y> tr = twisted_solve<Y>(parent, n, tau, pm, Wk, &gamma);
+    double nrm2 = to_d(tr.nrm2);
+    RepPtr<Y> P(parent, n);
+    Y s = -tau;
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        Y dp = P.D[i] + s;
+        if (ysmall(dp, pm)) dp = -pm;
+        double z = to_d(work[i]);
+        acc += fabs(to_d(dp)) * z * z;
+        if (i < n - 1) s = (P.LD[i] / dp) * P.L[i] * s - tau;
+    }
+    double r = acc / nrm2;
+    return isfinite(r) ? r : INFINITY;
+}
+
+// New RRR for a cluster (Algorithm 1, lines 15-17): a shift tau just outside
+// the left or right end of the cluster, child = parent - tau I by the
+// stationary transform in working precision.  Candidates back off from the
+// cluster by a growing distance, never beyond half the gap to the rest of
+// the spectrum (Sec. 3.2: a small gaptol leaves room to back off).  A
+// candidate is accepted when the element growth max |d+_i|, or else the
+// growth weighted by an approximate cluster vector, is at most
+// growth_k * spdiam(root).  If no candidate passes, the one with the
+// smallest weighted growth is taken (Sec. 2, "Requirements on the
+// representations"; Sec. 4.1) and counted in reps_failed.  Members move to
+// the child: rep, sigma += tau, brackets shifted by -tau (re-verified by the
+// refinement that follows).
+template <class Y>
+MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* blocks, Y* pool,
+                           const SolveCfg& cfg, DevCounters* C) {
+    const int n = K.n;
+    Item& first = items[K.a];
+    Item& last = items[K.b - 1];
+    const BlockDesc& B = blocks[first.block];
+    const Y* parent = (const Y*)first.rep;
+    Y pm = from_d<Y>(B.pivmin);
+    Y* child = pool + K.pool_off;
+    double lo = first.lo, hi = last.hi;
+    double span = hi - lo;
+    double bw = fmax(first.hi - first.lo, last.hi - last.lo);
+    double base = fmax(fmax(0.25 * span, 2.0 * bw), 4.0 * cfg.eps_y * fmax(fabs(lo), fabs(hi)));
+    base = fmax(base, 4.0 * B.pivmin);
+    const double bound = cfg.growth_k * B.spdiam;
+    double best_w = INFINITY, best_tau = lo - base;
+    bool accepted = false;
+    unsigned long long steps = 0;
+    for (int k = 0; k < 6 && !accepted; ++k) {
+        double delta = base * (double)(1 << k);
+        for (int side = 0; side < 2 && !accepted; ++side) {
+            double gap = side == 0 ? K.gapL : K.gapR;
+            if (k > 0 && delta > 0.5 * gap) continue;
+            double tau = side == 0 ? lo - delta : hi + delta;
+            double g = dstqds<Y>(parent, n, from_d<Y>(tau), pm, (Y*)nullptr);
+            steps += n;
+            if (g <= bound) {
+                best_tau = tau;
+                accepted = true;
+                break;
+            }
+            // child storage doubles as work space for the weighted test
+            double w = weighted_growth<Y>(parent, n, from_d<Y>(tau), pm, child);
+            steps += 3ULL * n;
+            if (w <= bound) {
+                best_tau = tau;
+                accepted = true;
+                break;
+            }
+            if (w < best_w) {
+                best_w = w;
+                best_tau = tau;
+            }
+        }
+    }
+    if (!accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
+    dstqds<Y>(parent, n, from_d<Y>(best_tau), pm, child);
+    steps += n;
+    MRRR_ATOMIC_ADD(&C->qd_steps_y, steps);
+    // sigma_child = sigma_parent + tau, kept as an unevaluated double pair
+    dd sig = dd(first.sig_hi, first.sig_lo) + dd(best_tau);
+    for (int u = K.a; u < K.b; ++u) {
+        Item& I = items[u];
+        I.rep = child;
+        I.sig_hi = sig.hi;
+        I.sig_lo = sig.lo;
+        I.lo = I.lo - best_tau;
+        I.hi = I.hi - best_tau;
+        I.depth = K.depth + 1;
+        I.kind = KIND_OPEN;
+    }
+    MRRR_ATOMIC_MAX(&C->d_max, K.depth + 1);
+}
+
+// --------------------------------------------------------------- a6 + a7: RQI and store
+
+// Rayleigh quotient iteration with twisted factorizations, guarded by
+// bisection (Algorithm 1, line 10; Sec. 2, "Rayleigh quotient iteration"):
+// each step solves at lambda, updates the bracket with the inertia of the
+// stationary part, and corrects lambda by gamma_r / ||z||^2.  It stops when
+// the residual |gamma_r| / ||z|| is below k_rs gap eps_x sqrt(n) (mixed,
+// Sec. 3.2) or k_rs gap n eps / gaptol (plain, Eq. 2.3), or when the
+// correction stagnates below 4 eps_y |lambda|.  If the correction leaves the
+// bracket or the step budget runs out, lambda is bisected to relative
+// accuracy eps_x sqrt(n) gaptol (mixed) / n eps (plain) and one twisted solve
+// gives the vector (Sec. 3.2, "Rayleigh quotient iteration").  The vector is
+// normalised, signed (largest entry positive), rounded to x and stored with
+// lambda + sigma (Algorithm 1, line 11; Sec. 3.3).
+template <class X, class Y>
+MRRR_HD void rqi_item(Item& I, const MatrixDesc* mats, const BlockDesc* blocks, const SolveCfg& cfg,
+                      const Scratch<Y>& Wk, DevCounters* C) {
+    typedef typename Acc<Y>::T A_t;
+    const MatrixDesc& M = mats[I.matrix];
+    const BlockDesc& B = blocks[I.block];
+    const int n = I.n;
+    const Y* rep = (const Y*)I.rep;
+    Y pm = from_d<Y>(B.pivmin);
+    const double sq = sqrt((double)n);
+    double gap = fmin(I.gapL, I.gapR);
+    if (!(gap < INFINITY)) gap = fmax(B.spdiam, 1e-300);
+    const double tol = cfg.mixed ? cfg.krs * gap * cfg.eps_x * sq : cfg.krs * gap * n * cfg.eps_y / cfg.gaptol;
+    Y lo = from_d<Y>(I.lo), hi = from_d<Y>(I.hi);
+    Y lam = (lo + hi) * from_d<Y>(0.5);
+    Y gamma = from_d<Y>(0.0);
+    TwistResult<Y> tr;
+    Y lam_out = lam;
+    bool conv = false;
+    int iters = 0;
+    unsigned long long steps = 0;
+    if (n == 1) {
+        Wk.A(0) = from_d<Y>(1.0);
+        tr.r = 0;
+        tr.nrm2 = A_t(1.0);
+        lam_out = from_d<Y>(0.0);
+        conv = true;
+    } else {
+        for (int it = 0; it < cfg.max_rqi; ++it) {
+            tr = twisted_solve<Y>(rep, n, lam, pm, Wk, &gamma);
+            steps += 2ULL * n;
+            ++iters;
+            if (tr.neg >= I.j) hi = bmin(hi, lam);
+            else lo = bmax(lo, lam);
+            double nrm2 = to_d(tr.nrm2);
+            double resid = fabs(to_d(gamma)) / sqrt(nrm2);
+            Y corr = gamma / Y(tr.nrm2);
+            if (resid <= tol || fabs(to_d(corr)) <= 4.0 * cfg.eps_y * fabs(to_d(lam))) {
+                lam_out = lam + corr;
+                conv = true;
+                break;
+            }
+            Y nl = lam + corr;
+            if (!(lo < nl && nl < hi)) break;  // left the bracket: fall back to bisection
+            lam = nl;
+        }
+        if (!conv) {
+            MRRR_ATOMIC_ADD(&C->fallbacks, 1);
+            double rt = cfg.mixed ? cfg.eps_x * sq * cfg.gaptol : n * cfg.eps_y;
+            rt = fmax(rt, 4.0 * cfg.eps_y);
+            steps += bisect_bracket<Y, Y>(rep, n, I.j, lo, hi, B.pivmin, rt, 1, 600);
+            lam = (lo + hi) * from_d<Y>(0.5);
+            tr = twisted_solve<Y>(rep, n, lam, pm, Wk, &gamma);
+            steps += 2ULL * n;
+            ++iters;
+            double nrm2 = to_d(tr.nrm2);
+            double resid = fabs(to_d(gamma)) / sqrt(nrm2);
+            lam_out = lam + gamma / Y(tr.nrm2);
+            conv = resid <= fmax(tol, 8.0 * cfg.eps_y * n * fabs(to_d(lam)));
+            if (!conv) MRRR_ATOMIC_ADD(&C->noconv, 1);
+        }
+    }
+    MRRR_ATOMIC_ADD(&C->rqi_iters, iters);
+    MRRR_ATOMIC_ADD(&C->qd_steps_y, steps);
+    // eigenvalue of T: (lambda + sigma) / scale
+    dd lt = dd(to_d(lam_out)) + dd(I.sig_hi, I.sig_lo);
+    if constexpr (std::is_same<Y, dd>::value) lt = lam_out + dd(I.sig_hi, I.sig_lo);
+    double lam_T = (lt.hi + lt.lo) / M.scale;
+    // normalise, fix the sign (largest entry positive), cast to x, store
+    A_t nrm = ysqrt(tr.nrm2);
+    int imax = 0;
+    double zmax = -1.0;
+    for (int i = 0; i < n; ++i) {
+        double z = fabs(to_d(Wk.A(i)));
+        if (z > zmax) {
+            zmax = z;
+            imax = i;
+        }
+    }
+    double sgn = to_d(Wk.A(imax)) < 0.0 ? -1.0 : 1.0;
+    X* Z = (X*)M.Z + (size_t)I.outcol * (size_t)M.ldz + B.mrow;
+    if constexpr (std::is_same<A_t, dd>::value) {
+        // double-double: divide in working precision, round once to x
+        for (int i = 0; i < n; ++i) {
+            A_t z = A_t(Wk.A(i)) / nrm;
+            Z[i] = (X)(sgn * to_d(z));
+        }
+    } else {
+        double inv = sgn / to_d(nrm);
+        for (int i = 0; i < n; ++i) Z[i] = (X)(to_d(Wk.A(i)) * inv);
+    }
+    ((X*)M.W)[I.outcol] = (X)lam_T;
+}
+
+// --------------------------------------------------------------- ordering of W
+
+// W must be ascending.  Eigenvalues of different blocks were placed by their
+// bracket midpoints; the final values can swap neighbours that lie within
+// rounding of each other.  Repair by insertion with column swaps.
+template <class X>
+MRRR_HD void sort_fix_matrix(MatrixDesc& M) {
+    X* W = (X*)M.W;
+    X* Z = (X*)M.Z;
+    for (int i = 1; i < M.kout; ++i) {
+        int j = i;
+        while (j > 0 && W[j] < W[j - 1]) {
+            X t = W[j]; W[j] = W[j - 1]; W[j - 1] = t;
+            X* c0 = Z + (size_t)j * M.ldz;
+            X* c1 = Z + (size_t)(j - 1) * M.ldz;
+            for (int r = 0; r < M.n; ++r) {
+                X v = c0[r]; c0[r] = c1[r]; c1[r] = v;
+            }
+            --j;
+        }
+    }
+}
+
+}  // namespace mrrr
