@@ -60,18 +60,37 @@ typedef enum {
     MRRR_ERR_NOREP = -7       /* informational: no candidate passed the representation test */
 } mrrr_status;
 
+/* Phases of a solve, indexing mrrr_stats.phase_ms. */
+enum {
+    MRRR_PHASE_PREP = 0,     /* scaling and splitting (a1) */
+    MRRR_PHASE_ROOT = 1,     /* root representations and eigenvalue items (a2) */
+    MRRR_PHASE_BISECT = 2,   /* initial eigenvalues by bisection (a3) */
+    MRRR_PHASE_CLASSIFY = 3, /* classification into singletons and clusters (a4) */
+    MRRR_PHASE_SHIFT = 4,    /* child representations of clusters (a5) */
+    MRRR_PHASE_REFINE = 5,   /* refinement of cluster eigenvalues (a5) */
+    MRRR_PHASE_RQI = 6,      /* Rayleigh quotient iteration, vectors, stores (a6, a7) */
+    MRRR_PHASE_FINISH = 7,   /* output ordering and zero fill */
+    MRRR_NPHASES = 8
+};
+
 /* Per-solve statistics (optional output). */
 typedef struct {
     int nblocks;          /* blocks after splitting (Sec. 3.2, Preprocessing) */
     int d_max;            /* depth of the representation tree (Sec. 2) */
     int nclusters;        /* clusters processed (Algorithm 1, lines 14-17) */
     int largest_cluster;  /* size of the largest cluster; rho = largest_cluster / n */
-    int reps_failed;      /* accepted representations that failed the growth test */
-    int rqi_iters;        /* Rayleigh quotient iterations, all eigenpairs */
+    int reps_failed;      /* clusters whose chosen representation failed both growth tests */
+    int rqi_iters;        /* Rayleigh quotient iterations (twisted solves), all eigenpairs */
     int fallbacks;        /* eigenpairs that needed the bisection fallback */
     int noconv;           /* eigenpairs that missed the stopping criterion */
-    long long qd_steps_y;   /* qd recurrence steps executed in working precision */
-    long long qd_steps_low; /* qd recurrence steps executed in a lower precision */
+    long long qd_bisect;  /* qd steps (one row of one transform) in the initial bisection */
+    long long qd_refine;  /* qd steps in the refinement bisection of cluster eigenvalues */
+    long long qd_rqi;     /* qd steps in the Rayleigh quotient iterations */
+    long long qd_shift;   /* qd steps in building child representations */
+    long long qd_low;     /* qd steps executed in a precision below the working precision */
+    int timed;            /* 1 if phase_ms / phase_launches were measured (MRRR_FLAG_TIMING) */
+    int phase_launches[MRRR_NPHASES]; /* kernel launches per phase */
+    double phase_ms[MRRR_NPHASES];    /* device time per phase (CUDA events on the solve's stream) */
 } mrrr_stats;
 
 /* Tuning parameters; a zero field selects the default given in brackets. */
@@ -91,6 +110,7 @@ typedef struct {
 /* Variant bits for mrrr_params.flags. */
 #define MRRR_FLAG_NO_LOWPREC_BISECT 1 /* never pre-bracket eigenvalues in a lower precision */
 #define MRRR_FLAG_IEEE_DIV 2          /* use correctly rounded division in the qd recurrences */
+#define MRRR_FLAG_TIMING 4            /* time every phase with CUDA events (fills stats->phase_ms) */
 
 /*
  * Single-precision input/output (x = binary32).  MRRR_MIXED computes in
@@ -112,6 +132,23 @@ int mrrr_solve_s(int n, const float* d, const float* e, mrrr_range range, float 
 int mrrr_solve_d(int n, const double* d, const double* e, mrrr_range range, double vl, double vu,
                  int il, int iu, mrrr_mode mode, const mrrr_params* params, int* m_out,
                  double* W, double* Z, int ldz, void* stream);
+
+/*
+ * Batched solve (all eigenpairs of each matrix, or the index range
+ * il[p]..iu[p] when il and iu are non-NULL): nb independent tridiagonals,
+ * each solved on its own (Algorithm 1 per matrix), in one sequence of
+ * launches over all matrices.  The arrays n, d, e, W, Z, ldz, il, iu,
+ * m_out and status are host arrays of length nb; every d[p], e[p], W[p],
+ * Z[p] must be a device pointer (n[p] = 1 needs no e[p]).  status[p]
+ * receives the matrix's own status and m_out[p] (may be NULL) its count.
+ * Returns 0 if every matrix succeeded, else the first failing status.
+ */
+int mrrr_solve_batch_s(int nb, const int* n, const float* const* d, const float* const* e, const int* il,
+                       const int* iu, mrrr_mode mode, const mrrr_params* params, int* m_out, float* const* W,
+                       float* const* Z, const int* ldz, int* status, void* stream);
+int mrrr_solve_batch_d(int nb, const int* n, const double* const* d, const double* const* e, const int* il,
+                       const int* iu, mrrr_mode mode, const mrrr_params* params, int* m_out, double* const* W,
+                       double* const* Z, const int* ldz, int* status, void* stream);
 
 /* Human-readable text for a status code (static storage). */
 const char* mrrr_strerror(int status);

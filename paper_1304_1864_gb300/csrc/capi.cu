@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "mrrr.h"
 #include "mrrr_entry.h"
@@ -150,9 +151,105 @@ int solve_one(int n, const X* d, const X* e, mrrr_range range, X vl, X vu, int i
     return rc;
 }
 
+template <class X>
+int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const int* il, const int* iu,
+               mrrr_mode mode, const mrrr_params* prm, int* m_out, X* const* W, X* const* Z, const int* ldz,
+               int* status, void* stream) {
+    const bool xs = std::is_same<X, float>::value;
+    if (nb < 0 || (nb > 0 && (!n || !d || !W || !Z || !ldz || !status))) return MRRR_ERR_ARG;
+    if (mode != MRRR_PLAIN && mode != MRRR_MIXED) return MRRR_ERR_ARG;
+    if ((il == nullptr) != (iu == nullptr)) return MRRR_ERR_ARG;
+    if (nb == 0) return MRRR_OK;
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+        cudaGetLastError();
+        return MRRR_ERR_CUDA;
+    }
+    std::vector<MatrixDesc> mats;
+    std::vector<int> map;  // mats index -> batch index
+    static const X zero1[1] = {X(0)};
+    X* dzero = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int p = 0; p < nb; ++p) {
+        status[p] = MRRR_OK;
+        if (m_out) m_out[p] = 0;
+        if (n[p] < 0 || (n[p] > 0 && (ldz[p] < n[p] || !d[p] || !W[p] || !Z[p] || (n[p] > 1 && !e[p])))) {
+            status[p] = MRRR_ERR_ARG;
+            continue;
+        }
+        if (il && (il[p] < 1 || iu[p] > n[p] || il[p] > iu[p])) {
+            status[p] = MRRR_ERR_ARG;
+            continue;
+        }
+        if (n[p] == 0) continue;
+        MatrixDesc M;
+        memset(&M, 0, sizeof(M));
+        M.d = d[p];
+        M.e = e ? (const void*)e[p] : nullptr;
+        M.W = W[p];
+        M.Z = Z[p];
+        M.ldz = ldz[p];
+        M.n = n[p];
+        M.range = il ? MRRR_INDEX : MRRR_ALL;
+        M.il = il ? il[p] : 1;
+        M.iu = il ? iu[p] : n[p];
+        if (n[p] == 1 || !M.e) {
+            if (!dzero) {
+                if (cudaMallocAsync((void**)&dzero, sizeof(X), st) != cudaSuccess) return MRRR_ERR_NOMEM;
+                if (cudaMemcpyAsync(dzero, zero1, sizeof(X), cudaMemcpyHostToDevice, st) != cudaSuccess)
+                    return MRRR_ERR_CUDA;
+            }
+            M.e = dzero;
+        }
+        mats.push_back(M);
+        map.push_back(p);
+    }
+    int rc = MRRR_OK;
+    if (!mats.empty()) {
+        SolveCfg cfg = make_cfg(xs, mode == MRRR_MIXED, prm);
+        int max_depth = (prm && prm->max_depth > 0) ? prm->max_depth : 16;
+        mrrr_stats* stats = prm ? prm->stats : nullptr;
+        if (stats) memset(stats, 0, sizeof(*stats));
+        int P = (int)mats.size();
+        if (xs)
+            rc = mode == MRRR_MIXED ? mrrr::solve_batch_s_mixed(P, mats.data(), cfg, max_depth, st, stats)
+                                    : mrrr::solve_batch_s_plain(P, mats.data(), cfg, max_depth, st, stats);
+        else
+            rc = mode == MRRR_MIXED ? mrrr::solve_batch_d_mixed(P, mats.data(), cfg, max_depth, st, stats)
+                                    : mrrr::solve_batch_d_plain(P, mats.data(), cfg, max_depth, st, stats);
+        for (int q = 0; q < P; ++q) {
+            int p = map[q];
+            int sp = mats[q].status;
+            status[p] = sp == mrrr::ST_ERR_NONFINITE ? MRRR_ERR_NONFINITE
+                        : sp == mrrr::ST_ERR_NOCONV  ? MRRR_ERR_NOCONV
+                                                     : (rc == MRRR_OK || rc == MRRR_ERR_NOCONV ? MRRR_OK : rc);
+            if (m_out) m_out[p] = mats[q].kout;
+        }
+    }
+    if (dzero) cudaFreeAsync(dzero, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MRRR_ERR_CUDA;
+    if (rc != MRRR_OK && rc != MRRR_ERR_NOCONV) return rc;
+    for (int p = 0; p < nb; ++p)
+        if (status[p] != MRRR_OK) return status[p];
+    return MRRR_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int mrrr_solve_batch_s(int nb, const int* n, const float* const* d, const float* const* e, const int* il,
+                       const int* iu, mrrr_mode mode, const mrrr_params* params, int* m_out, float* const* W,
+                       float* const* Z, const int* ldz, int* status, void* stream) {
+    return solve_many<float>(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, status, stream);
+}
+
+int mrrr_solve_batch_d(int nb, const int* n, const double* const* d, const double* const* e, const int* il,
+                       const int* iu, mrrr_mode mode, const mrrr_params* params, int* m_out, double* const* W,
+                       double* const* Z, const int* ldz, int* status, void* stream) {
+    return solve_many<double>(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, status, stream);
+}
+
 
 int mrrr_solve_s(int n, const float* d, const float* e, mrrr_range range, float vl, float vu, int il, int iu,
                  mrrr_mode mode, const mrrr_params* params, int* m_out, float* W, float* Z, int ldz, void* stream) {

@@ -147,10 +147,15 @@ MRRR_HD void root_block(BlockDesc& B, const MatrixDesc& M, const double* wd, con
         }
         ldl_factor<Y>(a, b, n, best_mu, best_side, rep);
         B.mu = best_mu;
-        perturb_and_derive<Y>(rep, n, cfg.xi, cfg.seed, 4ULL * (uint64_t)B.row0);
+        // xi is capped at eps_x n / 8 so that for tiny matrices the perturbation
+        // alone cannot exceed the accuracy target 2 n eps_x ||T||; the counter is
+        // keyed by the row within the matrix, so a matrix gets the same
+        // perturbation alone and inside a batch
+        double xi = fmin(cfg.xi, cfg.eps_x * (double)M.n / 8.0);
+        perturb_and_derive<Y>(rep, n, xi, cfg.seed, 4ULL * (uint64_t)B.mrow);
         // spectrum of M_root = T - mu I (perturbed by at most ~xi relative): pad the bracket
         double lo = gl - best_mu, hi = gu - best_mu;
-        double pad = (4.0 * cfg.xi + 8.0 * n * Prec<Y>::eps) * fmax(fabs(lo), fabs(hi)) + 4.0 * B.pivmin;
+        double pad = (4.0 * xi + 8.0 * n * Prec<Y>::eps) * fmax(fabs(lo), fabs(hi)) + 4.0 * B.pivmin;
         B.gl = lo - pad;
         B.gu = hi + pad;
     }
@@ -466,7 +471,7 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     if (!accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
     dstqds<Y>(parent, n, from_d<Y>(best_tau), pm, child);
     steps += n;
-    MRRR_ATOMIC_ADD(&C->qd_steps_y, steps);
+    MRRR_ATOMIC_ADD(&C->qd_shift, steps);
     // sigma_child = sigma_parent + tau, kept as an unevaluated double pair
     dd sig = dd(first.sig_hi, first.sig_lo) + dd(best_tau);
     for (int u = K.a; u < K.b; ++u) {
@@ -497,10 +502,10 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
 // normalised, signed (largest entry positive), rounded to x and stored with
 // lambda + sigma (Algorithm 1, line 11; Sec. 3.3).
 template <class X, class Y>
-MRRR_HD void rqi_item(Item& I, const MatrixDesc* mats, const BlockDesc* blocks, const SolveCfg& cfg,
+MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const SolveCfg& cfg,
                       const Scratch<Y>& Wk, DevCounters* C) {
     typedef typename Acc<Y>::T A_t;
-    const MatrixDesc& M = mats[I.matrix];
+    MatrixDesc& M = mats[I.matrix];
     const BlockDesc& B = blocks[I.block];
     const int n = I.n;
     const Y* rep = (const Y*)I.rep;
@@ -555,11 +560,14 @@ MRRR_HD void rqi_item(Item& I, const MatrixDesc* mats, const BlockDesc* blocks, 
             double resid = fabs(to_d(gamma)) / sqrt(nrm2);
             lam_out = lam + gamma / Y(tr.nrm2);
             conv = resid <= fmax(tol, 8.0 * cfg.eps_y * n * fabs(to_d(lam)));
-            if (!conv) MRRR_ATOMIC_ADD(&C->noconv, 1);
+            if (!conv) {
+                MRRR_ATOMIC_ADD(&C->noconv, 1);
+                M.status = ST_ERR_NOCONV;  // every writer stores the same value
+            }
         }
     }
     MRRR_ATOMIC_ADD(&C->rqi_iters, iters);
-    MRRR_ATOMIC_ADD(&C->qd_steps_y, steps);
+    MRRR_ATOMIC_ADD(&C->qd_rqi, steps);
     // eigenvalue of T: (lambda + sigma) / scale
     dd lt = dd(to_d(lam_out)) + dd(I.sig_hi, I.sig_lo);
     if constexpr (std::is_same<Y, dd>::value) lt = lam_out + dd(I.sig_hi, I.sig_lo);

@@ -93,14 +93,14 @@ __global__ void k_init_items(const int* blist, int nb, const BlockDesc* blocks, 
 
 template <class Y>
 __global__ void k_bisect(Item* items, const int* list, int count, const BlockDesc* blocks, double rtol,
-                         int verify, DevCounters* C) {
+                         int verify, unsigned long long* step_counter) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
     int it = list ? list[t] : t;
     Item& I = items[it];
     unsigned long long steps = 0;
     bisect_item<Y>(I, blocks[I.block].pivmin, rtol, verify, 200, &steps);
-    atomicAdd(&C->qd_steps_y, steps);
+    atomicAdd(step_counter, steps);
 }
 
 static __global__ void k_assign_cols(Item* items, int count, const MatrixDesc* mats, const BlockDesc* blocks) {
@@ -134,7 +134,7 @@ __global__ void k_shift(const Cluster* clusters, int nc, Item* items, const Bloc
 }
 
 template <class X, class Y>
-__global__ void k_rqi(Item* items, const int* list, int count, const MatrixDesc* mats, const BlockDesc* blocks,
+__global__ void k_rqi(Item* items, const int* list, int count, MatrixDesc* mats, const BlockDesc* blocks,
                       SolveCfg cfg, Y* scratch, int nmax, DevCounters* C) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
@@ -188,6 +188,47 @@ struct Arena {
     T* var = arena.alloc<T>(count);                     \
     if (!var) return MRRR_ERR_NOMEM
 
+// Optional per-phase device timing with CUDA events on the solve's stream.
+struct Timeline {
+    bool on;
+    cudaStream_t st;
+    struct Rec {
+        int phase, launches;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    cudaEvent_t cur_a = nullptr;
+    int cur = -1;
+    Timeline(bool enabled, cudaStream_t s) : on(enabled), st(s) {}
+    void begin(int phase) {
+        if (!on) return;
+        cudaEventCreate(&cur_a);
+        cudaEventRecord(cur_a, st);
+        cur = phase;
+    }
+    void end(int launches = 1) {
+        if (!on) return;
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, st);
+        recs.push_back({cur, launches, cur_a, b});
+    }
+    void collect(mrrr_stats* s) {
+        for (Rec& r : recs) {
+            float ms = 0.f;
+            if (s && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                s->phase_ms[r.phase] += ms;
+                s->phase_launches[r.phase] += r.launches;
+            }
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        recs.clear();
+        if (s) s->timed = on ? 1 : 0;
+    }
+    ~Timeline() { collect(nullptr); }
+};
+
 template <class Y> struct ScratchBudget {
     static size_t bytes() { return (size_t)4 << 30; }  // 4 GiB of RQI scratch per wave
 };
@@ -211,6 +252,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
     }
     if (N > (1LL << 30) / 4) return MRRR_ERR_ARG;
     Arena arena(st);
+    Timeline tl(stats && (cfg.flags & MRRR_FLAG_TIMING), st);
     MRRR_ALLOC(d_mats, MatrixDesc, P);
     MRRR_ALLOC(d_blocks, BlockDesc, N);
     MRRR_ALLOC(wd, double, N);
@@ -222,7 +264,9 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
     MRRR_CK(cudaMemcpyAsync(d_mats, mats, sizeof(MatrixDesc) * P, cudaMemcpyHostToDevice, st));
 
     // a1: scale + split
+    tl.begin(MRRR_PHASE_PREP);
     k_prep<X><<<P, 32, 0, st>>>(d_mats, d_blocks, wd, we, cfg);
+    tl.end();
     MRRR_CK(cudaGetLastError());
     MRRR_CK(cudaMemcpyAsync(mats, d_mats, sizeof(MatrixDesc) * P, cudaMemcpyDeviceToHost, st));
     MRRR_CK(cudaStreamSynchronize(st));
@@ -235,8 +279,10 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         MRRR_ALLOC(d_blist, int, NB);
         MRRR_CK(cudaMemcpyAsync(d_blist, blist.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, st));
         // a2: root representations
+        tl.begin(MRRR_PHASE_ROOT);
         k_root<Y><<<grid_for(NB), kThreads, 0, st>>>(d_blist, NB, d_blocks, d_mats, wd, we, reps, cfg);
         k_scan_items<<<1, 1024, 0, st>>>(d_blist, NB, d_blocks, d_mats, P, d_total);
+        tl.end(2);
         MRRR_CK(cudaGetLastError());
         int K = 0;
         MRRR_CK(cudaMemcpyAsync(&K, d_total, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -248,16 +294,28 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             MRRR_ALLOC(member_list, int, K);
             MRRR_ALLOC(clus_a, Cluster, K / 2 + 1);
             MRRR_ALLOC(clus_b, Cluster, K / 2 + 1);
+            tl.begin(MRRR_PHASE_ROOT);
             k_init_items<Y><<<grid_for(NB), kThreads, 0, st>>>(d_blist, NB, d_blocks, items, reps);
+            tl.end();
             // eigenvector columns of a split matrix are zero outside their block
+            tl.begin(MRRR_PHASE_FINISH);
+            int nz = 0;
             for (int p = 0; p < P; ++p) {
-                if (mats[p].nblocks > 1 && mats[p].kout > 0)
+                if (mats[p].nblocks > 1 && mats[p].kout > 0) {
                     MRRR_CK(cudaMemset2DAsync(mats[p].Z, sizeof(X) * (size_t)mats[p].ldz, 0,
                                               sizeof(X) * (size_t)mats[p].n, mats[p].kout, st));
+                    ++nz;
+                }
             }
+            tl.end(nz);
             // a3: initial eigenvalues by bisection on the root reps
-            k_bisect<Y><<<grid_for(K), kThreads, 0, st>>>(items, nullptr, K, d_blocks, cfg.rtol_class, 0, d_C);
+            tl.begin(MRRR_PHASE_BISECT);
+            k_bisect<Y><<<grid_for(K), kThreads, 0, st>>>(items, nullptr, K, d_blocks, cfg.rtol_class, 0,
+                                                          &d_C->qd_bisect);
+            tl.end();
+            tl.begin(MRRR_PHASE_CLASSIFY);
             k_assign_cols<<<grid_for(K), kThreads, 0, st>>>(items, K, d_mats, d_blocks);
+            tl.end();
             MRRR_CK(cudaGetLastError());
             // a4/a5: classification and the representation tree, level by level
             Cluster* groups = nullptr;
@@ -268,20 +326,26 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 MRRR_CK(cudaMemsetAsync(&d_C->ncluster, 0, 2 * sizeof(int), st));  // ncluster, nmember
                 bool force = level >= max_depth;
                 double gt = force ? -INFINITY : cfg.gaptol;
+                tl.begin(MRRR_PHASE_CLASSIFY);
                 if (level == 0)
                     k_classify_blocks<<<grid_for(NB), kThreads, 0, st>>>(d_blist, NB, d_blocks, items, gt,
                                                                          single_list, out, member_list, d_C);
                 else
                     k_classify_clusters<<<grid_for(ngroups), kThreads, 0, st>>>(groups, ngroups, items, gt,
                                                                                 single_list, out, member_list, d_C);
+                tl.end();
                 MRRR_CK(cudaGetLastError());
                 MRRR_CK(cudaMemcpyAsync(&C, d_C, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
                 MRRR_CK(cudaStreamSynchronize(st));
                 if (C.ncluster == 0) break;
                 MRRR_ALLOC(pool, Y, (size_t)C.pool_need);
+                tl.begin(MRRR_PHASE_SHIFT);
                 k_shift<Y><<<grid_for(C.ncluster), kThreads, 0, st>>>(out, C.ncluster, items, d_blocks, pool, cfg, d_C);
+                tl.end();
+                tl.begin(MRRR_PHASE_REFINE);
                 k_bisect<Y><<<grid_for(C.nmember), kThreads, 0, st>>>(items, member_list, C.nmember, d_blocks,
-                                                                      cfg.rtol_class, 1, d_C);
+                                                                      cfg.rtol_class, 1, &d_C->qd_refine);
+                tl.end();
                 MRRR_CK(cudaGetLastError());
                 groups = out;
                 ngroups = C.ncluster;
@@ -296,19 +360,24 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 MRRR_ALLOC(scratch, Y, (size_t)wave * 2 * nmax);
                 for (long long s0 = 0; s0 < S; s0 += wave) {
                     int cnt = (int)std::min<long long>(wave, S - s0);
+                    tl.begin(MRRR_PHASE_RQI);
                     k_rqi<X, Y><<<grid_for(cnt), kThreads, 0, st>>>(items, single_list + s0, cnt, d_mats, d_blocks,
                                                                     cfg, scratch, nmax, d_C);
+                    tl.end();
                     MRRR_CK(cudaGetLastError());
                 }
             }
+            tl.begin(MRRR_PHASE_FINISH);
             k_sort_fix<X><<<grid_for(P, 32), 32, 0, st>>>(d_mats, P);
+            tl.end();
             MRRR_CK(cudaGetLastError());
         }
     }
     MRRR_CK(cudaMemcpyAsync(&C, d_C, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    MRRR_CK(cudaMemcpyAsync(mats, d_mats, sizeof(MatrixDesc) * P, cudaMemcpyDeviceToHost, st));
     MRRR_CK(cudaStreamSynchronize(st));
     int rc = 0;
-    for (int p = 0; p < P; ++p) {
+    for (int p = 0; p < P && rc == 0; ++p) {
         if (mats[p].status == ST_ERR_NONFINITE) rc = MRRR_ERR_NONFINITE;
     }
     if (rc == 0 && C.noconv > 0) rc = MRRR_ERR_NOCONV;
@@ -321,8 +390,12 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         stats->rqi_iters = C.rqi_iters;
         stats->fallbacks = C.fallbacks;
         stats->noconv = C.noconv;
-        stats->qd_steps_y = (long long)C.qd_steps_y;
-        stats->qd_steps_low = (long long)C.qd_steps_low;
+        stats->qd_bisect = (long long)C.qd_bisect;
+        stats->qd_refine = (long long)C.qd_refine;
+        stats->qd_rqi = (long long)C.qd_rqi;
+        stats->qd_shift = (long long)C.qd_shift;
+        stats->qd_low = (long long)C.qd_steps_low;
+        tl.collect(stats);
     }
     if (arena.failed) return MRRR_ERR_NOMEM;
     return rc;

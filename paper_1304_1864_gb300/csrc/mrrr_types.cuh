@@ -93,7 +93,10 @@ struct Cluster {
 };
 
 struct DevCounters {
-    unsigned long long qd_steps_y;
+    unsigned long long qd_bisect;  // qd steps (one row of one transform) in the initial bisection
+    unsigned long long qd_refine;  // ... in the refinement bisection of cluster eigenvalues
+    unsigned long long qd_rqi;     // ... in the Rayleigh quotient iterations (incl. fallbacks)
+    unsigned long long qd_shift;   // ... in building child representations
     unsigned long long qd_steps_low;
     unsigned long long pool_need;  // pool elements requested at the current level
     int nsingle;        // singletons appended to the singleton list
