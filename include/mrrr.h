@@ -87,7 +87,8 @@ typedef struct {
     long long qd_refine;  /* qd steps in the refinement bisection of cluster eigenvalues */
     long long qd_rqi;     /* qd steps in the Rayleigh quotient iterations */
     long long qd_shift;   /* qd steps in building child representations */
-    long long qd_low;     /* qd steps executed in a precision below the working precision */
+    long long qd_low;     /* qd steps of the pre-bisection in a precision below the working one */
+    int verify_fail;      /* pre-bisection brackets widened by the working-precision check */
     int timed;            /* 1 if phase_ms / phase_launches were measured (MRRR_FLAG_TIMING) */
     int phase_launches[MRRR_NPHASES]; /* kernel launches per phase */
     double phase_ms[MRRR_NPHASES];    /* device time per phase (CUDA events on the solve's stream) */

@@ -26,7 +26,7 @@ class MrrrStats(ctypes.Structure):
                 ("largest_cluster", ctypes.c_int), ("reps_failed", ctypes.c_int), ("rqi_iters", ctypes.c_int),
                 ("fallbacks", ctypes.c_int), ("noconv", ctypes.c_int),
                 ("qd_bisect", ctypes.c_longlong), ("qd_refine", ctypes.c_longlong), ("qd_rqi", ctypes.c_longlong),
-                ("qd_shift", ctypes.c_longlong), ("qd_low", ctypes.c_longlong),
+                ("qd_shift", ctypes.c_longlong), ("qd_low", ctypes.c_longlong), ("verify_fail", ctypes.c_int),
                 ("timed", ctypes.c_int), ("phase_launches", ctypes.c_int * NPHASES),
                 ("phase_ms", ctypes.c_double * NPHASES)]
 

@@ -89,19 +89,20 @@ MRRR_HD void prep_matrix(MatrixDesc& M, BlockDesc* blocks, double* wd, double* w
 
 // --------------------------------------------------------------- a2: root representation
 
-// Root representation (Algorithm 1, lines 1-2): Gershgorin interval, shift
-// mu just outside one end so that T - mu I is definite (Sec. 3.2, the root
+// Root representation (Algorithm 1, lines 1-2): Gershgorin interval, a shift
+// mu just outside one end so that T - mu I is definite (Sec. 3.2: a root
 // representation is always found "by making T - mu I definite"), LDL^T in
-// working precision, random relative perturbation, derived LD and LLD.
-// Also decides which local indices the block computes.
+// working precision, random relative perturbation, derived LD and LLD, and a
+// rounded low-precision copy for the pre-bisection.  Split into steps so a
+// CTA can run the two candidate factorizations on two warps and the
+// element-wise work on all its threads.
+
+// Step 1 (one thread): Gershgorin bounds, pivmin, spectral diameter.
 template <class Y>
-MRRR_HD void root_block(BlockDesc& B, const MatrixDesc& M, const double* wd, const double* we, Y* reps,
-                        const SolveCfg& cfg) {
+MRRR_HD void root_bounds(BlockDesc& B, const double* wd, const double* we, double* gl_out, double* gu_out) {
     const int n = B.n;
     const double* a = wd + B.row0;
     const double* b = we + B.row0;
-    Y* rep = reps + 4 * (size_t)B.row0;
-    B.rep_off = 4 * B.row0;
     double gl = 0.0, gu = 0.0, emax2 = 0.0;
     for (int i = 0; i < n; ++i) {
         double r = 0.0;
@@ -114,68 +115,120 @@ MRRR_HD void root_block(BlockDesc& B, const MatrixDesc& M, const double* wd, con
         if (i == 0 || lo < gl) gl = lo;
         if (i == 0 || hi > gu) gu = hi;
     }
-    B.pivmin = Prec<Y>::tiny * fmax(1.0, emax2);
-    double bnd = fmax(fabs(gl), fabs(gu));
+    // 4x the smallest normal of the working precision keeps every reciprocal
+    // of a guarded pivot finite
+    B.pivmin = 4.0 * Prec<Y>::tiny * fmax(1.0, emax2);
     B.spdiam = gu - gl;
-    if (n == 1) {
-        B.mu = a[0];
-        rep[0] = from_d<Y>(0.0);
-        rep[1] = rep[2] = rep[3] = from_d<Y>(0.0);
-        B.gl = 0.0;
-        B.gu = 0.0;
-    } else {
-        // try both ends with a growing safety margin; keep the smaller growth
-        double best = INFINITY;
-        int best_side = 0;
-        double best_mu = 0.0;
-        double delta = 4.0 * n * 1.1102230246251565e-16 * bnd + 4.0 * B.pivmin;
-        for (int attempt = 0; attempt < 40 && !(best < INFINITY); ++attempt) {
-            double muL = gl - delta, muR = gu + delta;
-            double gL = ldl_factor<Y>(a, b, n, muL, +1, rep);
-            double gR = ldl_factor<Y>(a, b, n, muR, -1, rep);
-            if (gL <= gR && gL < INFINITY) {
-                best = gL; best_side = +1; best_mu = muL;
-            } else if (gR < INFINITY) {
-                best = gR; best_side = -1; best_mu = muR;
-            }
-            delta *= 16.0;
+    *gl_out = gl;
+    *gu_out = gu;
+}
+
+// Step 2 (one thread per side): factor T - mu I with mu = gl - delta (side 0,
+// positive definite, into the D/L slots) or mu = gu + delta (side 1,
+// negative definite, into the LD/LLD slots), growing delta until definite.
+template <class Y>
+MRRR_HD double root_candidate(const BlockDesc& B, const double* wd, const double* we, Y* reps, double gl,
+                              double gu, int side, double* mu_out) {
+    const int n = B.n;
+    Y* rep = reps + 4 * (size_t)B.row0 + (side ? 2 * (size_t)n : 0);
+    double bnd = fmax(fabs(gl), fabs(gu));
+    double delta = 4.0 * n * 1.1102230246251565e-16 * bnd + 4.0 * B.pivmin;
+    for (int attempt = 0; attempt < 40; ++attempt) {
+        double mu = side ? gu + delta : gl - delta;
+        double g = ldl_factor<Y>(wd + B.row0, we + B.row0, n, mu, side ? -1 : +1, rep);
+        if (g < INFINITY) {
+            *mu_out = mu;
+            return g;
         }
-        if (!(best < INFINITY)) {
-            // cannot happen for finite scaled input; fall back to an indefinite left shift
-            best_mu = gl - delta;
-            best_side = +1;
-        }
-        ldl_factor<Y>(a, b, n, best_mu, best_side, rep);
-        B.mu = best_mu;
-        // xi is capped at eps_x n / 8 so that for tiny matrices the perturbation
-        // alone cannot exceed the accuracy target 2 n eps_x ||T||; the counter is
-        // keyed by the row within the matrix, so a matrix gets the same
-        // perturbation alone and inside a batch
-        double xi = fmin(cfg.xi, cfg.eps_x * (double)M.n / 8.0);
-        perturb_and_derive<Y>(rep, n, xi, cfg.seed, 4ULL * (uint64_t)B.mrow);
-        // spectrum of M_root = T - mu I (perturbed by at most ~xi relative): pad the bracket
-        double lo = gl - best_mu, hi = gu - best_mu;
-        double pad = (4.0 * xi + 8.0 * n * Prec<Y>::eps) * fmax(fabs(lo), fabs(hi)) + 4.0 * B.pivmin;
-        B.gl = lo - pad;
-        B.gu = hi + pad;
+        delta *= 16.0;
     }
-    // which eigenvalues to compute
+    *mu_out = side ? gu + delta : gl - delta;
+    return INFINITY;
+}
+
+// Step 3 (one thread): choose the side with the smaller growth, set mu, the
+// bracket of the root spectrum, and the perturbation bound.
+MRRR_HD void root_choose(BlockDesc& B, const MatrixDesc& M, double gl, double gu, double gL, double muL, double gR,
+                         double muR, const SolveCfg& cfg) {
+    const int n = B.n;
+    bool right = !(gL <= gR) && gR < INFINITY;
+    if (!(gL < INFINITY) && !(gR < INFINITY)) right = false;  // cannot happen for finite scaled input
+    B.side = right ? -1 : +1;
+    B.mu = right ? muR : muL;
+    B.growth = right ? gR : gL;
+    // xi is capped at eps_x n / 8 so that for tiny matrices the perturbation
+    // alone cannot exceed the accuracy target 2 n eps_x ||T||
+    double xi = fmin(cfg.xi, cfg.eps_x * (double)M.n / 8.0);
+    double lo = gl - B.mu, hi = gu - B.mu;
+    double pad = (4.0 * xi + 8.0 * n * cfg.eps_y) * fmax(fabs(lo), fabs(hi)) + 4.0 * B.pivmin;
+    B.gl = lo - pad;
+    B.gu = hi + pad;
+}
+
+// Step 4 (element i, after step 3): move the right-end candidate into place.
+template <class Y>
+MRRR_HD void root_move(const BlockDesc& B, Y* reps, int i) {
+    if (B.side > 0) return;
+    const int n = B.n;
+    Y* rep = reps + 4 * (size_t)B.row0;
+    rep[i] = rep[2 * n + i];
+    if (i < n - 1) rep[n + i] = rep[3 * n + i];
+}
+
+// Step 5 (element i, after step 4): multiply d_i and l_i by (1 + xi r) with r
+// uniform in [-1, 1) from the counter-based generator (Algorithm 1, line 2;
+// Sec. 3.2, "Random perturbations"), form LD_i, LLD_i and the low copy.  The
+// counter is keyed by the row within the matrix, so a matrix is perturbed
+// identically alone and inside a batch.
+template <class Y, class Lo>
+MRRR_HD void root_element(const BlockDesc& B, const MatrixDesc& M, Y* reps, Lo* reps_lo, int i,
+                          const SolveCfg& cfg) {
+    const int n = B.n;
+    Y* rep = reps + 4 * (size_t)B.row0;
+    Lo* lo = reps_lo + 2 * (size_t)B.row0;
+    double xi = fmin(cfg.xi, cfg.eps_x * (double)M.n / 8.0);
+    uint64_t c0 = 4ULL * (uint64_t)B.mrow + 2ULL * (uint64_t)i;
+    Y d = rep[i];
+    Y l = (i < n - 1) ? rep[n + i] : from_d<Y>(0.0);
+    if (xi > 0.0) {
+        d = d + d * from_d<Y>(xi * sym_uniform(cfg.seed, c0));
+        if (i < n - 1) l = l + l * from_d<Y>(xi * sym_uniform(cfg.seed, c0 + 1ULL));
+    }
+    rep[i] = d;
+    Y ld = d * l;
+    Y lld = ld * l;
+    if (i < n - 1) {
+        rep[n + i] = l;
+        rep[2 * n + i] = ld;
+        rep[3 * n + i] = lld;
+    } else {
+        rep[2 * n - 1] = from_d<Y>(0.0);
+        rep[3 * n - 1] = from_d<Y>(0.0);
+        rep[4 * n - 1] = from_d<Y>(0.0);
+    }
+    lo[i] = (Lo)to_d(d);
+    lo[n + i] = (Lo)to_d(lld);
+}
+
+// Step 6 (one thread, after step 5): which eigenvalues the block computes.
+template <class Y>
+MRRR_HD void root_range(BlockDesc& B, const MatrixDesc& M, const double* wd, const Y* reps) {
+    const int n = B.n;
+    const Y* rep = reps + 4 * (size_t)B.row0;
     int wlo = 1, whi = n;
     if (M.range == RANGE_INDEX && M.nblocks == 1) {
         wlo = M.il;
         whi = M.iu;
     } else if (M.range == RANGE_VALUE) {
         if (n == 1) {
-            double lam = a[0];
+            double lam = wd[B.row0];
             bool in = lam > M.vl * M.scale && lam <= M.vu * M.scale;
             wlo = 1;
             whi = in ? 1 : 0;
         } else {
             Y pm = from_d<Y>(B.pivmin);
-            int cl = negcount<Y>(rep, rep + 3 * n, n, from_d<Y>(M.vl * M.scale - B.mu), pm);
-            int cu = negcount<Y>(rep, rep + 3 * n, n, from_d<Y>(M.vu * M.scale - B.mu), pm);
-            wlo = cl + 1;
-            whi = cu;
+            wlo = negcount<Y>(rep, rep + 3 * n, n, from_d<Y>(M.vl * M.scale - B.mu), pm) + 1;
+            whi = negcount<Y>(rep, rep + 3 * n, n, from_d<Y>(M.vu * M.scale - B.mu), pm);
         }
     }
     B.w_lo = wlo;
@@ -190,30 +243,50 @@ MRRR_HD void root_block(BlockDesc& B, const MatrixDesc& M, const double* wd, con
     B.nitems = B.f_hi >= B.f_lo ? B.f_hi - B.f_lo + 1 : 0;
 }
 
-// Create the items of one block (after the host assigned item0).
-template <class Y>
-MRRR_HD void init_block_items(const BlockDesc& B, int bidx, Item* items, const Y* reps) {
-    for (int t = 0; t < B.nitems; ++t) {
-        Item& I = items[B.item0 + t];
-        I.j = B.f_lo + t;
-        I.lo = B.gl;
-        I.hi = B.gu;
-        I.gapL = INFINITY;
-        I.gapR = INFINITY;
-        I.sig_hi = B.mu;
-        I.sig_lo = 0.0;
-        I.rep = reps + B.rep_off;
-        I.n = B.n;
-        I.block = bidx;
-        I.matrix = B.matrix;
-        I.outcol = -1;
-        I.depth = 0;
-        I.kind = KIND_OPEN;
-        I.wanted = (I.j >= B.w_lo && I.j <= B.w_hi) ? 1 : 0;  // wanted (refined by assign_cols)
-    }
+// A block of size one: its eigenvalue is d_1 exactly (mu = d_1, rep = 0).
+template <class Y, class Lo>
+MRRR_HD void root_trivial(BlockDesc& B, const double* wd, Y* reps, Lo* reps_lo) {
+    Y* rep = reps + 4 * (size_t)B.row0;
+    Lo* lo = reps_lo + 2 * (size_t)B.row0;
+    B.mu = wd[B.row0];
+    B.side = +1;
+    B.growth = 0.0;
+    rep[0] = rep[1] = rep[2] = rep[3] = from_d<Y>(0.0);
+    lo[0] = lo[1] = Lo(0);
+    B.gl = 0.0;
+    B.gu = 0.0;
+}
+
+// Item t of one block (after the host-side scan assigned item0).
+template <class Y, class Lo>
+MRRR_HD void init_item(const BlockDesc& B, int bidx, Item& I, int t, const Y* reps, const Lo* reps_lo) {
+    I.j = B.f_lo + t;
+    I.lo = B.gl;
+    I.hi = B.gu;
+    I.gapL = INFINITY;
+    I.gapR = INFINITY;
+    I.sig_hi = B.mu;
+    I.sig_lo = 0.0;
+    I.rep = reps + 4 * (size_t)B.row0;
+    I.rep_lo = reps_lo + 2 * (size_t)B.row0;
+    I.n = B.n;
+    I.block = bidx;
+    I.matrix = B.matrix;
+    I.outcol = -1;
+    I.depth = 0;
+    I.kind = KIND_OPEN;
+    I.wanted = (I.j >= B.w_lo && I.j <= B.w_hi) ? 1 : 0;  // refined by assign_col
 }
 
 // --------------------------------------------------------------- a3: bisection
+
+// Relative separation of two neighbouring brackets (Sec. 2, reldist).
+MRRR_HD double reldist(const Item& A, const Item& B) {
+    double den = fmax(fmax(fabs(A.lo), fabs(A.hi)), fmax(fabs(B.lo), fabs(B.hi)));
+    double num = B.lo - A.hi;
+    return den > 0.0 ? num / den : INFINITY;
+}
+
 
 template <class T> MRRR_HD T bmax(const T& a, const T& b) { return a < b ? b : a; }
 template <class T> MRRR_HD T bmin(const T& a, const T& b) { return b < a ? b : a; }
@@ -282,6 +355,92 @@ MRRR_HD void bisect_item(Item& I, double pivmin, double rtol, int verify, int ma
     if (steps_out) *steps_out += s;
 }
 
+// Pre-bisection in the low precision on the rounded copy of the rep (Sec.
+// 3.2, "Arithmetic used to approximate eigenvalues": bisection on a copy M_x
+// in faster arithmetic), down to relative width `wrel`.  Nothing is trusted
+// yet: verify_endpoint re-checks both ends in the working precision.
+template <class Lo>
+MRRR_HD unsigned long long bisect_lo_item(Item& I, double pivmin, double wrel, int max_steps) {
+    const int n = I.n;
+    if (n == 1) return 0;
+    const Lo* D = (const Lo*)I.rep_lo;
+    const Lo* LLD = D + n;
+    Lo pm = (Lo)fmax(pivmin, (double)Prec<Lo>::tiny * 4.0);
+    double lo = I.lo, hi = I.hi;
+    unsigned long long steps = 0;
+    for (int it = 0; it < max_steps; ++it) {
+        if (!(hi - lo > wrel * fmax(fabs(lo), fabs(hi)))) break;
+        double mid = 0.5 * (lo + hi);
+        Lo m = (Lo)mid;
+        if (!((double)m > lo && (double)m < hi)) break;  // no representable point inside
+        ++steps;
+        if (negcount_lo<Lo>(D, LLD, n, m, pm) >= I.j) hi = (double)m;
+        else lo = (double)m;
+    }
+    I.lo = lo;
+    I.hi = hi;
+    return steps * (unsigned long long)n;
+}
+
+// Re-establish one end of the bracket in the working precision: side 0 needs
+// negcount(lo) < j, side 1 needs negcount(hi) >= j.  A failing end is moved
+// outward by a doubling step; after 8 failures it jumps to the bound of the
+// whole root spectrum in the item's coordinates.  Returns qd steps; *fails
+// counts the widenings.
+template <class Y>
+MRRR_HD unsigned long long verify_endpoint(Item& I, const BlockDesc& B, int side, int* fails) {
+    const int n = I.n;
+    if (n == 1) return 0;
+    const Y* rep = (const Y*)I.rep;
+    const Y* D = rep;
+    const Y* LLD = rep + 3 * n;
+    Y pm = from_d<Y>(B.pivmin);
+    double x = side ? I.hi : I.lo;
+    double w = fmax(fmax(I.hi - I.lo, 4.0 * Prec<double>::eps * fabs(x)), 4.0 * B.pivmin);
+    unsigned long long steps = 0;
+    int f = 0;
+    for (int it = 0; it < 64; ++it) {
+        ++steps;
+        int c = negcount<Y>(D, LLD, n, from_d<Y>(x), pm);
+        bool ok = side ? (c >= I.j) : (c < I.j);
+        if (ok) break;
+        ++f;
+        if (f > 8) {
+            // shift of this rep relative to the root: sigma - mu
+            double off = (I.sig_hi - B.mu) + I.sig_lo;
+            double pad = 4.0 * Prec<double>::eps * (fabs(B.gl) + fabs(B.gu) + fabs(off)) + 4.0 * B.pivmin;
+            double bound = side ? (B.gu - off + pad) : (B.gl - off - pad);
+            if (side ? (bound > x) : (bound < x)) {
+                x = bound;
+                continue;
+            }
+        }
+        x = side ? x + w : x - w;
+        w *= 2.0;
+    }
+    if (side) I.hi = x;
+    else I.lo = x;
+    *fails += f;
+    return steps * (unsigned long long)n;
+}
+
+// An item is certified when, for each neighbour in the same rep, the
+// verified brackets already give reldist >= gaptol (Sec. 2 notes that the
+// relative-accuracy requirement can be relaxed for eigenvalues with a large
+// gap); such items skip the working-precision refinement.  Neighbours in
+// another rep lie outside the current cluster and were separated by gaptol
+// one level up.
+MRRR_HD bool certified(int t, const Item* items, int count_all, double gaptol) {
+    const Item& I = items[t];
+    if (t > 0 && items[t - 1].rep == I.rep && items[t - 1].block == I.block) {
+        if (!(reldist(items[t - 1], I) >= gaptol)) return false;
+    }
+    if (t + 1 < count_all && items[t + 1].rep == I.rep && items[t + 1].block == I.block) {
+        if (!(reldist(I, items[t + 1]) >= gaptol)) return false;
+    }
+    return true;
+}
+
 // --------------------------------------------------------------- output columns
 
 // Output column of item t: position of its eigenvalue among the wanted
@@ -315,11 +474,6 @@ MRRR_HD void assign_col(int t, Item* items, const MatrixDesc* mats, const BlockD
 
 // --------------------------------------------------------------- a4: classification
 
-MRRR_HD double reldist(const Item& A, const Item& B) {
-    double den = fmax(fmax(fabs(A.lo), fabs(A.hi)), fmax(fabs(B.lo), fabs(B.hi)));
-    double num = B.lo - A.hi;
-    return den > 0.0 ? num / den : INFINITY;
-}
 
 // Partition the items [a, b) that share one rep (Algorithm 1, line 7): j and
 // j+1 are separated when reldist(j, j+1) >= gaptol (Sec. 2, "Classification
@@ -404,7 +558,7 @@ MRRR_HD double weighted_growth(const Y* parent, int n, Y tau, Y pm, Y* work) {
         if (ysmall(dp, pm)) dp = -pm;
         double z = to_d(work[i]);
         acc += fabs(to_d(dp)) * z * z;
-        if (i < n - 1) s = (P.LD[i] / dp) * P.L[i] * s - tau;
+        if (i < n - 1) s = qdiv<Y>(P.LD[i], dp) * P.L[i] * s - tau;
     }
     double r = acc / nrm2;
     return isfinite(r) ? r : INFINITY;
@@ -420,10 +574,10 @@ MRRR_HD double weighted_growth(const Y* parent, int n, Y tau, Y pm, Y* work) {
 // growth_k * spdiam(root).  If no candidate passes, the one with the
 // smallest weighted growth is taken (Sec. 2, "Requirements on the
 // representations"; Sec. 4.1) and counted in reps_failed.  Members move to
-// the child: rep, sigma += tau, brackets shifted by -tau (re-verified by the
-// refinement that follows).
-template <class Y>
-MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* blocks, Y* pool,
+// the child: rep (and its low-precision copy), sigma += tau, brackets
+// shifted by -tau (re-verified by the refinement that follows).
+template <class Y, class Lo>
+MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* blocks, Y* pool, Lo* pool_lo,
                            const SolveCfg& cfg, DevCounters* C) {
     const int n = K.n;
     Item& first = items[K.a];
@@ -432,6 +586,7 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     const Y* parent = (const Y*)first.rep;
     Y pm = from_d<Y>(B.pivmin);
     Y* child = pool + K.pool_off;
+    Lo* child_lo = pool_lo + K.pool_off / 2;
     double lo = first.lo, hi = last.hi;
     double span = hi - lo;
     double bw = fmax(first.hi - first.lo, last.hi - last.lo);
@@ -439,6 +594,7 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     base = fmax(base, 4.0 * B.pivmin);
     const double bound = cfg.growth_k * B.spdiam;
     double best_w = INFINITY, best_tau = lo - base;
+    double stored_tau = NAN;  // the candidate whose child rep is in `child`
     bool accepted = false;
     unsigned long long steps = 0;
     for (int k = 0; k < 6 && !accepted; ++k) {
@@ -447,7 +603,10 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
             double gap = side == 0 ? K.gapL : K.gapR;
             if (k > 0 && delta > 0.5 * gap) continue;
             double tau = side == 0 ? lo - delta : hi + delta;
-            double g = dstqds<Y>(parent, n, from_d<Y>(tau), pm, (Y*)nullptr);
+            // the first candidate is usually accepted: build it in place
+            bool store = (k == 0 && side == 0);
+            double g = dstqds<Y>(parent, n, from_d<Y>(tau), pm, store ? child : (Y*)nullptr);
+            if (store) stored_tau = tau;
             steps += n;
             if (g <= bound) {
                 best_tau = tau;
@@ -456,6 +615,7 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
             }
             // child storage doubles as work space for the weighted test
             double w = weighted_growth<Y>(parent, n, from_d<Y>(tau), pm, child);
+            stored_tau = NAN;
             steps += 3ULL * n;
             if (w <= bound) {
                 best_tau = tau;
@@ -469,14 +629,21 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
         }
     }
     if (!accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
-    dstqds<Y>(parent, n, from_d<Y>(best_tau), pm, child);
-    steps += n;
+    if (!(stored_tau == best_tau)) {
+        dstqds<Y>(parent, n, from_d<Y>(best_tau), pm, child);
+        steps += n;
+    }
+    for (int i = 0; i < n; ++i) {
+        child_lo[i] = (Lo)to_d(child[i]);
+        child_lo[n + i] = (Lo)to_d(child[3 * n + i]);
+    }
     MRRR_ATOMIC_ADD(&C->qd_shift, steps);
     // sigma_child = sigma_parent + tau, kept as an unevaluated double pair
     dd sig = dd(first.sig_hi, first.sig_lo) + dd(best_tau);
     for (int u = K.a; u < K.b; ++u) {
         Item& I = items[u];
         I.rep = child;
+        I.rep_lo = child_lo;
         I.sig_hi = sig.hi;
         I.sig_lo = sig.lo;
         I.lo = I.lo - best_tau;

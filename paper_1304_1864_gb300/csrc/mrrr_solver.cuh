@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -21,6 +22,11 @@ inline int grid_for(long long n, int threads = kThreads) { return (int)((n + thr
 
 // ------------------------------------------------------------------ kernels
 
+// Low precision used for the pre-bisection under each working precision.
+template <class Y> struct LowOf { typedef float T; static constexpr bool use = false; };
+template <> struct LowOf<double> { typedef float T; static constexpr bool use = true; };
+template <> struct LowOf<dd> { typedef double T; static constexpr bool use = true; };
+
 template <class X>
 __global__ void k_prep(MatrixDesc* mats, BlockDesc* blocks, double* wd, double* we, SolveCfg cfg) {
     int p = blockIdx.x;
@@ -30,19 +36,42 @@ __global__ void k_prep(MatrixDesc* mats, BlockDesc* blocks, double* wd, double* 
     for (int b = 0; b < M.nblocks; ++b) blocks[M.row0 + b].matrix = p;
 }
 
-template <class Y>
-__global__ void k_root(const int* blist, int nb, BlockDesc* blocks, const MatrixDesc* mats, const double* wd,
-                       const double* we, Y* reps, SolveCfg cfg) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nb) return;
-    BlockDesc& B = blocks[blist[t]];
-    root_block<Y>(B, mats[B.matrix], wd, we, reps, cfg);
+// One CTA per block: the two candidate factorizations run on two warps, the
+// perturbation and derived data on all threads.
+template <class Y, class Lo>
+__global__ void k_root(const int* blist, BlockDesc* blocks, const MatrixDesc* mats, const double* wd,
+                       const double* we, Y* reps, Lo* reps_lo, SolveCfg cfg) {
+    __shared__ double s_gl, s_gu, s_g[2], s_mu[2];
+    BlockDesc& B = blocks[blist[blockIdx.x]];
+    const MatrixDesc& M = mats[B.matrix];
+    const int n = B.n;
+    if (threadIdx.x == 0) root_bounds<Y>(B, wd, we, &s_gl, &s_gu);
+    __syncthreads();
+    if (n == 1) {
+        if (threadIdx.x == 0) {
+            root_trivial<Y, Lo>(B, wd, reps, reps_lo);
+            root_range<Y>(B, M, wd, reps);
+        }
+        return;
+    }
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+        int side = threadIdx.x == 32;
+        s_g[side] = root_candidate<Y>(B, wd, we, reps, s_gl, s_gu, side, &s_mu[side]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) root_choose(B, M, s_gl, s_gu, s_g[0], s_mu[0], s_g[1], s_mu[1], cfg);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) root_move<Y>(B, reps, i);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) root_element<Y, Lo>(B, M, reps, reps_lo, i, cfg);
+    __syncthreads();
+    if (threadIdx.x == 0) root_range<Y>(B, M, wd, reps);
 }
 
 // Exclusive scan of the item counts over the block list (one CTA), plus the
 // per-matrix totals: item range, number of returned eigenpairs.
 static __global__ void k_scan_items(const int* blist, int nb, BlockDesc* blocks, MatrixDesc* mats, int nmat,
-                             int* total_out) {
+                                    int* total_out) {
     __shared__ int part[1024];
     const int T = blockDim.x;
     int per = (nb + T - 1) / T;
@@ -84,23 +113,70 @@ static __global__ void k_scan_items(const int* blist, int nb, BlockDesc* blocks,
     }
 }
 
-template <class Y>
-__global__ void k_init_items(const int* blist, int nb, const BlockDesc* blocks, Item* items, const Y* reps) {
+// One thread per item; the block is found by binary search over the item
+// offsets (ascending in block-list order).
+template <class Y, class Lo>
+__global__ void k_init_items(const int* blist, int nb, const BlockDesc* blocks, Item* items, int K, const Y* reps,
+                             const Lo* reps_lo) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nb) return;
-    init_block_items<Y>(blocks[blist[t]], blist[t], items, reps);
+    if (t >= K) return;
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (blocks[blist[mid]].item0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    // skip blocks without items that share the same offset
+    while (lo + 1 < nb && blocks[blist[lo]].nitems == 0) ++lo;
+    const BlockDesc& B = blocks[blist[lo]];
+    init_item<Y, Lo>(B, blist[lo], items[t], t - B.item0, reps, reps_lo);
 }
 
 template <class Y>
-__global__ void k_bisect(Item* items, const int* list, int count, const BlockDesc* blocks, double rtol,
-                         int verify, unsigned long long* step_counter) {
+__global__ void k_bisect(Item* items, const int* list, int count, const int* count_dev, const BlockDesc* blocks,
+                         double rtol, int verify, unsigned long long* step_counter) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (count_dev) count = *count_dev;
     if (t >= count) return;
     int it = list ? list[t] : t;
     Item& I = items[it];
     unsigned long long steps = 0;
     bisect_item<Y>(I, blocks[I.block].pivmin, rtol, verify, 200, &steps);
-    atomicAdd(step_counter, steps);
+    if (steps) atomicAdd(step_counter, steps);
+}
+
+template <class Lo>
+__global__ void k_bisect_lo(Item* items, const int* list, int count, const BlockDesc* blocks, double wrel,
+                            DevCounters* C) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    Item& I = items[list ? list[t] : t];
+    unsigned long long s = bisect_lo_item<Lo>(I, blocks[I.block].pivmin, wrel, 200);
+    if (s) atomicAdd(&C->qd_steps_low, s);
+}
+
+// Two threads per item: one per end of the bracket.
+template <class Y>
+__global__ void k_verify(Item* items, const int* list, int count, const BlockDesc* blocks, DevCounters* C,
+                         unsigned long long* step_counter) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * count) return;
+    Item& I = items[list ? list[t >> 1] : (t >> 1)];
+    int fails = 0;
+    unsigned long long s = verify_endpoint<Y>(I, blocks[I.block], t & 1, &fails);
+    if (s) atomicAdd(step_counter, s);
+    if (fails) atomicAdd(&C->verify_fail, fails);
+}
+
+static __global__ void k_certify(const Item* items, int K, const int* list, int count, double gaptol,
+                                 int* refine_list, DevCounters* C) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    int it = list ? list[t] : t;
+    if (!certified(it, items, K, gaptol)) {
+        int slot = atomicAdd(&C->nrefine, 1);
+        refine_list[slot] = it;
+    }
 }
 
 static __global__ void k_assign_cols(Item* items, int count, const MatrixDesc* mats, const BlockDesc* blocks) {
@@ -109,8 +185,9 @@ static __global__ void k_assign_cols(Item* items, int count, const MatrixDesc* m
     assign_col(t, items, mats, blocks);
 }
 
-static __global__ void k_classify_blocks(const int* blist, int nb, const BlockDesc* blocks, Item* items, double gaptol,
-                                  int* single_list, Cluster* clusters, int* member_list, DevCounters* C) {
+static __global__ void k_classify_blocks(const int* blist, int nb, const BlockDesc* blocks, Item* items,
+                                         double gaptol, int* single_list, Cluster* clusters, int* member_list,
+                                         DevCounters* C) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nb) return;
     const BlockDesc& B = blocks[blist[t]];
@@ -118,19 +195,19 @@ static __global__ void k_classify_blocks(const int* blist, int nb, const BlockDe
     classify_group(B.item0, B.item0 + B.nitems, items, gaptol, single_list, clusters, member_list, C);
 }
 
-static __global__ void k_classify_clusters(const Cluster* groups, int ng, Item* items, double gaptol, int* single_list,
-                                    Cluster* clusters, int* member_list, DevCounters* C) {
+static __global__ void k_classify_clusters(const Cluster* groups, int ng, Item* items, double gaptol,
+                                           int* single_list, Cluster* clusters, int* member_list, DevCounters* C) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ng) return;
     classify_group(groups[t].a, groups[t].b, items, gaptol, single_list, clusters, member_list, C);
 }
 
-template <class Y>
-__global__ void k_shift(const Cluster* clusters, int nc, Item* items, const BlockDesc* blocks, Y* pool,
+template <class Y, class Lo>
+__global__ void k_shift(const Cluster* clusters, int nc, Item* items, const BlockDesc* blocks, Y* pool, Lo* pool_lo,
                         SolveCfg cfg, DevCounters* C) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nc) return;
-    shift_cluster<Y>(clusters[t], items, blocks, pool, cfg, C);
+    shift_cluster<Y, Lo>(clusters[t], items, blocks, pool, pool_lo, cfg, C);
 }
 
 template <class X, class Y>
@@ -200,17 +277,17 @@ struct Timeline {
     cudaEvent_t cur_a = nullptr;
     int cur = -1;
     Timeline(bool enabled, cudaStream_t s) : on(enabled), st(s) {}
-    void begin(int phase) {
+    void begin(int phase, cudaStream_t s = nullptr) {
         if (!on) return;
         cudaEventCreate(&cur_a);
-        cudaEventRecord(cur_a, st);
+        cudaEventRecord(cur_a, s ? s : st);
         cur = phase;
     }
-    void end(int launches = 1) {
+    void end(int launches = 1, cudaStream_t s = nullptr) {
         if (!on) return;
         cudaEvent_t b;
         cudaEventCreate(&b);
-        cudaEventRecord(b, st);
+        cudaEventRecord(b, s ? s : st);
         recs.push_back({cur, launches, cur_a, b});
     }
     void collect(mrrr_stats* s) {
@@ -229,6 +306,36 @@ struct Timeline {
     ~Timeline() { collect(nullptr); }
 };
 
+// A second stream for work that may overlap the main stream; joined back
+// into the main stream before the owner's allocations are released.
+struct SideStream {
+    cudaStream_t main;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    explicit SideStream(cudaStream_t m) : main(m) {}
+    bool start() {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return false;
+        if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return false;
+        if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) return false;
+        if (cudaEventRecord(fork, main) != cudaSuccess) return false;
+        return cudaStreamWaitEvent(s, fork, 0) == cudaSuccess;
+    }
+    void rejoin() {
+        if (!s) return;
+        cudaEventRecord(join, s);
+        cudaStreamWaitEvent(main, join, 0);
+    }
+    ~SideStream() {
+        if (s) {
+            rejoin();
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+    }
+};
+
 template <class Y> struct ScratchBudget {
     static size_t bytes() { return (size_t)4 << 30; }  // 4 GiB of RQI scratch per wave
 };
@@ -240,6 +347,10 @@ template <class Y> struct ScratchBudget {
 template <class X, class Y>
 int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
                 mrrr_stats* stats) {
+    typedef typename LowOf<Y>::T Lo;
+    const bool use_low = LowOf<Y>::use;
+    // relative width of the low-precision pre-bisection
+    const double wrel_lo = std::is_same<Lo, float>::value ? 0x1p-19 : cfg.rtol_class;
     long long N = 0;
     int nmax = 1;
     for (int p = 0; p < P; ++p) {
@@ -252,12 +363,14 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
     }
     if (N > (1LL << 30) / 4) return MRRR_ERR_ARG;
     Arena arena(st);
+    SideStream side(st);  // destroyed (joined) before the arena frees
     Timeline tl(stats && (cfg.flags & MRRR_FLAG_TIMING), st);
     MRRR_ALLOC(d_mats, MatrixDesc, P);
     MRRR_ALLOC(d_blocks, BlockDesc, N);
     MRRR_ALLOC(wd, double, N);
     MRRR_ALLOC(we, double, N);
     MRRR_ALLOC(reps, Y, 4 * N);
+    MRRR_ALLOC(reps_lo, Lo, 2 * N);
     MRRR_ALLOC(d_C, DevCounters, 1);
     MRRR_ALLOC(d_total, int, 1);
     MRRR_CK(cudaMemsetAsync(d_C, 0, sizeof(DevCounters), st));
@@ -280,7 +393,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         MRRR_CK(cudaMemcpyAsync(d_blist, blist.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, st));
         // a2: root representations
         tl.begin(MRRR_PHASE_ROOT);
-        k_root<Y><<<grid_for(NB), kThreads, 0, st>>>(d_blist, NB, d_blocks, d_mats, wd, we, reps, cfg);
+        k_root<Y, Lo><<<NB, 64, 0, st>>>(d_blist, d_blocks, d_mats, wd, we, reps, reps_lo, cfg);
         k_scan_items<<<1, 1024, 0, st>>>(d_blist, NB, d_blocks, d_mats, P, d_total);
         tl.end(2);
         MRRR_CK(cudaGetLastError());
@@ -292,10 +405,11 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             MRRR_ALLOC(items, Item, K);
             MRRR_ALLOC(single_list, int, K);
             MRRR_ALLOC(member_list, int, K);
+            MRRR_ALLOC(refine_list, int, K);
             MRRR_ALLOC(clus_a, Cluster, K / 2 + 1);
             MRRR_ALLOC(clus_b, Cluster, K / 2 + 1);
             tl.begin(MRRR_PHASE_ROOT);
-            k_init_items<Y><<<grid_for(NB), kThreads, 0, st>>>(d_blist, NB, d_blocks, items, reps);
+            k_init_items<Y, Lo><<<grid_for(K), kThreads, 0, st>>>(d_blist, NB, d_blocks, items, K, reps, reps_lo);
             tl.end();
             // eigenvector columns of a split matrix are zero outside their block
             tl.begin(MRRR_PHASE_FINISH);
@@ -308,18 +422,59 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 }
             }
             tl.end(nz);
-            // a3: initial eigenvalues by bisection on the root reps
-            tl.begin(MRRR_PHASE_BISECT);
-            k_bisect<Y><<<grid_for(K), kThreads, 0, st>>>(items, nullptr, K, d_blocks, cfg.rtol_class, 0,
-                                                          &d_C->qd_bisect);
-            tl.end();
+            // a3: initial eigenvalues (Algorithm 1, line 3): low-precision
+            // pre-bisection, verification of both bracket ends and refinement of
+            // the items not yet certified, in the working precision
+            auto approximate = [&](const int* list, int count, bool verify_ws, unsigned long long* ctr,
+                                   int phase) -> int {
+                tl.begin(phase);
+                int launches = 0;
+                if (use_low) {
+                    k_bisect_lo<Lo><<<grid_for(count), kThreads, 0, st>>>(items, list, count, d_blocks, wrel_lo, d_C);
+                    k_verify<Y><<<grid_for(2LL * count), kThreads, 0, st>>>(items, list, count, d_blocks, d_C, ctr);
+                    MRRR_CK(cudaMemsetAsync(&d_C->nrefine, 0, sizeof(int), st));
+                    k_certify<<<grid_for(count), kThreads, 0, st>>>(items, K, list, count, cfg.gaptol, refine_list,
+                                                                    d_C);
+                    k_bisect<Y><<<grid_for(count), kThreads, 0, st>>>(items, refine_list, count, &d_C->nrefine,
+                                                                       d_blocks, cfg.rtol_class, 0, ctr);
+                    launches = 4;
+                } else {
+                    k_bisect<Y><<<grid_for(count), kThreads, 0, st>>>(items, list, count, nullptr, d_blocks,
+                                                                       cfg.rtol_class, verify_ws ? 1 : 0, ctr);
+                    launches = 1;
+                }
+                tl.end(launches);
+                return cudaGetLastError() == cudaSuccess ? 0 : MRRR_ERR_CUDA;
+            };
+            if (approximate(nullptr, K, false, &d_C->qd_bisect, MRRR_PHASE_BISECT)) return MRRR_ERR_CUDA;
             tl.begin(MRRR_PHASE_CLASSIFY);
             k_assign_cols<<<grid_for(K), kThreads, 0, st>>>(items, K, d_mats, d_blocks);
             tl.end();
             MRRR_CK(cudaGetLastError());
-            // a4/a5: classification and the representation tree, level by level
+            size_t per = 2 * (size_t)nmax * sizeof(Y);
+            auto run_rqi = [&](int s0, int s1, cudaStream_t rs) -> int {
+                if (s1 <= s0) return 0;
+                long long wave = (long long)(ScratchBudget<Y>::bytes() / 2 / per);
+                wave = std::max<long long>(32, wave / 32 * 32);
+                wave = std::min<long long>(wave, ((long long)(s1 - s0) + 31) / 32 * 32);
+                Y* scratch = arena.alloc<Y>((size_t)wave * 2 * nmax);
+                if (!scratch) return MRRR_ERR_NOMEM;
+                for (long long w0 = s0; w0 < s1; w0 += wave) {
+                    int cnt = (int)std::min<long long>(wave, s1 - w0);
+                    tl.begin(MRRR_PHASE_RQI, rs);
+                    k_rqi<X, Y><<<grid_for(cnt), kThreads, 0, rs>>>(items, single_list + w0, cnt, d_mats, d_blocks,
+                                                                    cfg, scratch, nmax, d_C);
+                    tl.end(1, rs);
+                    if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
+                }
+                return 0;
+            };
+            // a4/a5: classification and the representation tree, level by level;
+            // the singletons of the root level go to a second stream so their
+            // RQI overlaps the (latency-bound) cluster levels
             Cluster* groups = nullptr;
             int ngroups = 0;
+            int s_root = -1;
             for (int level = 0;; ++level) {
                 Cluster* out = (level % 2 == 0) ? clus_a : clus_b;
                 MRRR_CK(cudaMemsetAsync(&d_C->pool_need, 0, sizeof(unsigned long long), st));
@@ -337,36 +492,35 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 MRRR_CK(cudaGetLastError());
                 MRRR_CK(cudaMemcpyAsync(&C, d_C, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
                 MRRR_CK(cudaStreamSynchronize(st));
+                if (level == 0) {
+                    s_root = C.nsingle;
+                    if (C.ncluster > 0 && s_root > 0) {
+                        if (!side.start()) return MRRR_ERR_CUDA;
+                        int rc = run_rqi(0, s_root, side.s);
+                        if (rc) return rc;
+                    } else {
+                        s_root = 0;  // everything runs on the main stream below
+                    }
+                }
                 if (C.ncluster == 0) break;
                 MRRR_ALLOC(pool, Y, (size_t)C.pool_need);
+                MRRR_ALLOC(pool_lo, Lo, (size_t)C.pool_need / 2);
                 tl.begin(MRRR_PHASE_SHIFT);
-                k_shift<Y><<<grid_for(C.ncluster), kThreads, 0, st>>>(out, C.ncluster, items, d_blocks, pool, cfg, d_C);
-                tl.end();
-                tl.begin(MRRR_PHASE_REFINE);
-                k_bisect<Y><<<grid_for(C.nmember), kThreads, 0, st>>>(items, member_list, C.nmember, d_blocks,
-                                                                      cfg.rtol_class, 1, &d_C->qd_refine);
+                k_shift<Y, Lo><<<grid_for(C.ncluster), kThreads, 0, st>>>(out, C.ncluster, items, d_blocks, pool,
+                                                                          pool_lo, cfg, d_C);
                 tl.end();
                 MRRR_CK(cudaGetLastError());
+                if (approximate(member_list, C.nmember, true, &d_C->qd_refine, MRRR_PHASE_REFINE))
+                    return MRRR_ERR_CUDA;
                 groups = out;
                 ngroups = C.ncluster;
             }
-            // a6/a7: RQI for every singleton, in waves bounded by the scratch budget
-            const int S = C.nsingle;
-            if (S > 0) {
-                size_t per = 2 * (size_t)nmax * sizeof(Y);
-                long long wave = (long long)(ScratchBudget<Y>::bytes() / per);
-                wave = std::max<long long>(32, wave / 32 * 32);
-                wave = std::min<long long>(wave, ((long long)S + 31) / 32 * 32);
-                MRRR_ALLOC(scratch, Y, (size_t)wave * 2 * nmax);
-                for (long long s0 = 0; s0 < S; s0 += wave) {
-                    int cnt = (int)std::min<long long>(wave, S - s0);
-                    tl.begin(MRRR_PHASE_RQI);
-                    k_rqi<X, Y><<<grid_for(cnt), kThreads, 0, st>>>(items, single_list + s0, cnt, d_mats, d_blocks,
-                                                                    cfg, scratch, nmax, d_C);
-                    tl.end();
-                    MRRR_CK(cudaGetLastError());
-                }
+            // a6/a7: RQI for the remaining singletons
+            {
+                int rc = run_rqi(s_root, C.nsingle, st);
+                if (rc) return rc;
             }
+            side.rejoin();
             tl.begin(MRRR_PHASE_FINISH);
             k_sort_fix<X><<<grid_for(P, 32), 32, 0, st>>>(d_mats, P);
             tl.end();
@@ -395,6 +549,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         stats->qd_rqi = (long long)C.qd_rqi;
         stats->qd_shift = (long long)C.qd_shift;
         stats->qd_low = (long long)C.qd_steps_low;
+        stats->verify_fail = C.verify_fail;
         tl.collect(stats);
     }
     if (arena.failed) return MRRR_ERR_NOMEM;

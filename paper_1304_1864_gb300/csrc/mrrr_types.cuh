@@ -58,6 +58,8 @@ struct BlockDesc {
     double gl, gu;      // bracket of the root rep's spectrum
     double spdiam;      // spectral diameter bound (Gershgorin width)
     double pivmin;      // pivot guard
+    int side;           // +1: root shift at the left end (positive definite), -1: right end
+    double growth;      // max |d_i| of the root factorization
     int w_lo, w_hi;     // wanted local indices (1-based, inclusive; w_lo > w_hi: none)
     int f_lo, f_hi;     // computed local indices (wanted plus one neighbour each side)
     int item0, nitems;
@@ -70,6 +72,7 @@ struct Item {
     double gapL, gapR;  // absolute distance to the neighbouring eigenvalues (left/right)
     double sig_hi, sig_lo;  // accumulated shift sigma of the current rep (hi + lo)
     const void* rep;    // current rep [D | L | LD | LLD], working precision
+    const void* rep_lo; // rounded copy [D | LLD] of the rep in the low precision (pre-bisection)
     int n;              // rep (block) size
     int j;              // 1-based index within the block
     int block;
@@ -110,6 +113,8 @@ struct DevCounters {
     int largest_cluster;
     int d_max;
     int forced;
+    int verify_fail;    // low-precision brackets that failed verification and were widened
+    int nrefine;        // items needing working-precision refinement at the current step
 };
 
 }  // namespace mrrr

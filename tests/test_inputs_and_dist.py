@@ -1,0 +1,86 @@
+"""CPU checks of the synthetic input generators and of the multi-rank timing
+helper of bench.py (two gloo ranks)."""
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1304_1864_gb300 import inputs
+
+
+def test_generators_follow_their_definitions():
+    d, e = inputs.wilkinson(7)
+    assert list(d) == [3, 2, 1, 0, 1, 2, 3] and np.all(e == 1)
+    d, e = inputs.clement(5)
+    assert np.all(d == 0) and np.allclose(e, np.sqrt([4, 6, 6, 4]))
+    d, e = inputs.one_two_one(4)
+    assert np.all(d == 2) and np.all(e == -1)
+    d, e = inputs.hermite(4)
+    assert np.allclose(e, np.sqrt([0.5, 1.0, 1.5]))
+    d, e = inputs.glued_wilkinson(3, 5, 1e-8)
+    assert d.size == 15 and e[4] == 1e-8 and e[9] == 1e-8 and e[3] == 1
+    with pytest.raises(ValueError):
+        inputs.wilkinson(4)
+
+
+def test_uniform_is_seeded_and_reproducible():
+    a = inputs.uniform_random(100, 0)
+    b = inputs.uniform_random(100, 0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    rng = np.random.default_rng(0)
+    assert np.array_equal(a[0], rng.uniform(-1, 1, 100))
+    assert np.all(np.abs(a[0]) <= 1) and a[1].size == 99
+
+
+def test_workload_shapes():
+    c2 = inputs.workload_c2()
+    assert [d.size for d, _ in c2] == [4001, 4001, 4001]
+    (d3, e3), = inputs.workload_c3()
+    assert d3.size == 8040 and np.sum(e3 == 1e-8) == 39
+    batch = inputs.workload_c4(count=64)
+    ns = [d.size for _, d, _ in batch]
+    assert len(batch) == 64 and min(ns) >= 20 and max(ns) <= 2048
+    assert {k for k, _, _ in batch} <= set(inputs.BATCH_KINDS)
+
+
+def test_serving_trace():
+    tr = inputs.serving_trace(rate=200.0, seconds=2.0, seed=5)
+    assert 300 < len(tr) < 500
+    ts = [r["t"] for r in tr]
+    assert ts == sorted(ts) and ts[-1] < 2.0
+    for r in tr:
+        assert 64 <= r["n"] <= 16384 and 1 <= r["il"] <= r["iu"] <= r["n"]
+        if r["iu"] - r["il"] + 1 != r["n"]:
+            assert r["iu"] - r["il"] + 1 == math.ceil(0.1 * r["n"])
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    v = bench._max_over_ranks(float(rank + 1) * 10.0, world)
+    bench._barrier(world)
+    q.put((rank, v))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = [q.get(timeout=120) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert sorted(out) == [(0, 20.0), (1, 20.0)]
