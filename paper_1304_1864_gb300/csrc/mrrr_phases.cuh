@@ -4,6 +4,7 @@
 #pragma once
 
 #include "mrrr_core.cuh"
+#include "mrrr_fast.cuh"
 #include "mrrr_types.cuh"
 
 #include <type_traits>
@@ -280,12 +281,17 @@ MRRR_HD void init_item(const BlockDesc& B, int bidx, Item& I, int t, const Y* re
 
 // --------------------------------------------------------------- a3: bisection
 
-// Relative separation of two neighbouring brackets (Sec. 2, reldist).
-MRRR_HD double reldist(const Item& A, const Item& B) {
+// Relative separation of two neighbouring brackets (Sec. 2, reldist):
+// reldist(A, B) >= gaptol for neighbouring brackets A < B, evaluated
+// without a division (the denominator is >= 0); gaptol = -inf separates all.
+MRRR_HD bool separated(const Item& A, const Item& B, double gaptol) {
+    if (gaptol == -INFINITY) return true;
     double den = fmax(fmax(fabs(A.lo), fabs(A.hi)), fmax(fabs(B.lo), fabs(B.hi)));
-    double num = B.lo - A.hi;
-    return den > 0.0 ? num / den : INFINITY;
+    return (B.lo - A.hi) >= gaptol * den;
 }
+
+// Neighbouring items belong to the same group when they share a rep.
+MRRR_HD bool same_group(const Item& A, const Item& B) { return A.rep == B.rep && A.block == B.block; }
 
 
 template <class T> MRRR_HD T bmax(const T& a, const T& b) { return a < b ? b : a; }
@@ -293,6 +299,16 @@ template <class T> MRRR_HD T bmin(const T& a, const T& b) { return b < a ? b : a
 MRRR_HD double babs(double x) { return fabs(x); }
 MRRR_HD dd babs(const dd& x) { return dd_abs(x); }
 MRRR_HD float babs(float x) { return fabsf(x); }
+
+// Sturm count for bisection: the tuned binary64 count on the device when
+// FAST (classification brackets), the fully accurate one otherwise.
+template <class Y, bool FAST>
+MRRR_HD int count_at(const Y* D, const Y* LLD, int n, Y tau, Y pm) {
+#if defined(__CUDA_ARCH__)
+    if constexpr (FAST && std::is_same<Y, double>::value) return negcount_fast(D, LLD, n, tau, pm);
+#endif
+    return negcount<Y>(D, LLD, n, tau, pm);
+}
 
 // Bisection for eigenvalue j (1-based) of the rep on the bracket [lo, hi]
 // (Algorithm 1, lines 3 and 16; Sec. 2, "Classification of the
@@ -303,7 +319,7 @@ MRRR_HD float babs(float x) { return fabsf(x); }
 // from the parent's by the mixed relative perturbation of the shift).
 // The bracket type Bt is double for classification and the working
 // precision for the bisection fallback of the RQI.  Returns qd steps.
-template <class Y, class Bt>
+template <class Y, class Bt, bool FAST = false>
 MRRR_HD unsigned long long bisect_bracket(const Y* rep, int n, int j, Bt& lo, Bt& hi, double pivmin, double rtol,
                                           int verify, int max_steps) {
     const Y* D = rep;
@@ -317,10 +333,10 @@ MRRR_HD unsigned long long bisect_bracket(const Y* rep, int n, int j, Bt& lo, Bt
             for (int it = 0; it < 200; ++it) {
                 ++steps;
                 if (side == 0) {
-                    if (negcount<Y>(D, LLD, n, Y(lo), pm) < j) break;
+                    if (count_at<Y, FAST>(D, LLD, n, Y(lo), pm) < j) break;
                     lo = lo - w;
                 } else {
-                    if (negcount<Y>(D, LLD, n, Y(hi), pm) >= j) break;
+                    if (count_at<Y, FAST>(D, LLD, n, Y(hi), pm) >= j) break;
                     hi = hi + w;
                 }
                 w = w + w;
@@ -334,7 +350,7 @@ MRRR_HD unsigned long long bisect_bracket(const Y* rep, int n, int j, Bt& lo, Bt
         Bt mid = (lo + hi) * Bt(0.5);
         if (!(lo < mid && mid < hi)) break;
         ++steps;
-        if (negcount<Y>(D, LLD, n, Y(mid), pm) >= j) hi = mid;
+        if (count_at<Y, FAST>(D, LLD, n, Y(mid), pm) >= j) hi = mid;
         else lo = mid;
     }
     return steps * (unsigned long long)n;
@@ -349,7 +365,8 @@ MRRR_HD void bisect_item(Item& I, double pivmin, double rtol, int verify, int ma
         return;
     }
     double lo = I.lo, hi = I.hi;
-    unsigned long long s = bisect_bracket<Y, double>((const Y*)I.rep, I.n, I.j, lo, hi, pivmin, rtol, verify, max_steps);
+    unsigned long long s =
+        bisect_bracket<Y, double, true>((const Y*)I.rep, I.n, I.j, lo, hi, pivmin, rtol, verify, max_steps);
     I.lo = lo;
     I.hi = hi;
     if (steps_out) *steps_out += s;
@@ -401,7 +418,7 @@ MRRR_HD unsigned long long verify_endpoint(Item& I, const BlockDesc& B, int side
     int f = 0;
     for (int it = 0; it < 64; ++it) {
         ++steps;
-        int c = negcount<Y>(D, LLD, n, from_d<Y>(x), pm);
+        int c = count_at<Y, true>(D, LLD, n, from_d<Y>(x), pm);
         bool ok = side ? (c >= I.j) : (c < I.j);
         if (ok) break;
         ++f;
@@ -432,12 +449,8 @@ MRRR_HD unsigned long long verify_endpoint(Item& I, const BlockDesc& B, int side
 // one level up.
 MRRR_HD bool certified(int t, const Item* items, int count_all, double gaptol) {
     const Item& I = items[t];
-    if (t > 0 && items[t - 1].rep == I.rep && items[t - 1].block == I.block) {
-        if (!(reldist(items[t - 1], I) >= gaptol)) return false;
-    }
-    if (t + 1 < count_all && items[t + 1].rep == I.rep && items[t + 1].block == I.block) {
-        if (!(reldist(I, items[t + 1]) >= gaptol)) return false;
-    }
+    if (t > 0 && same_group(items[t - 1], I) && !separated(items[t - 1], I, gaptol)) return false;
+    if (t + 1 < count_all && same_group(I, items[t + 1]) && !separated(I, items[t + 1], gaptol)) return false;
     return true;
 }
 
@@ -475,61 +488,64 @@ MRRR_HD void assign_col(int t, Item* items, const MatrixDesc* mats, const BlockD
 // --------------------------------------------------------------- a4: classification
 
 
-// Partition the items [a, b) that share one rep (Algorithm 1, line 7): j and
-// j+1 are separated when reldist(j, j+1) >= gaptol (Sec. 2, "Classification
-// of the eigenvalues").  Singletons get their gaps and go to the singleton
-// list; clusters with at least one wanted member are appended to the cluster
-// list together with their members.
-MRRR_HD void classify_group(int a, int b, Item* items, double gaptol, int* single_list, Cluster* clusters,
-                            int* member_list, DevCounters* C) {
-    int s = a;
-    while (s < b) {
-        int e = s + 1;
-        while (e < b && reldist(items[e - 1], items[e]) < gaptol) ++e;
-        // run [s, e)
-        double gL = (s > a) ? items[s].lo - items[s - 1].hi : items[s].gapL;
-        double gR = (e < b) ? items[e].lo - items[e - 1].hi : items[e - 1].gapR;
-        if (e - s == 1) {
-            Item& I = items[s];
-            double mid = 0.5 * (I.lo + I.hi);
-            I.gapL = (s > a) ? mid - items[s - 1].hi : I.gapL;
-            I.gapR = (e < b) ? items[e].lo - mid : I.gapR;
+// Partition (Algorithm 1, line 7), one thread per item: j and j+1 of the
+// same rep are separated when reldist(j, j+1) >= gaptol (Sec. 2,
+// "Classification of the eigenvalues").  The first item of every run acts:
+// a run of one is a singleton (gaps recorded, appended to the singleton list
+// if wanted); a longer run with a wanted member becomes a cluster (appended
+// with its members and its outer gaps).  Other threads only read neighbours'
+// brackets, so the partition is race-free.
+MRRR_HD void classify_item(int t, Item* items, int K, double gaptol, int* single_list, Cluster* clusters,
+                           int* member_list, DevCounters* C) {
+    Item& I = items[t];
+    bool has_l = t > 0 && same_group(items[t - 1], I);
+    bool has_r = t + 1 < K && same_group(I, items[t + 1]);
+    if (has_l && !separated(items[t - 1], I, gaptol)) return;  // inside a run
+    bool cut_r = !has_r || separated(I, items[t + 1], gaptol);
+    if (cut_r) {
+        double mid = 0.5 * (I.lo + I.hi);
+        if (has_l) I.gapL = mid - items[t - 1].hi;
+        if (has_r) I.gapR = items[t + 1].lo - mid;
+        if (I.wanted) {
             I.kind = KIND_SINGLETON;
-            if (I.wanted) {
-                int slot = MRRR_ATOMIC_ADD(&C->nsingle, 1);
-                single_list[slot] = s;
-            } else {
-                I.kind = KIND_DROPPED;
-            }
+            int slot = MRRR_ATOMIC_ADD(&C->nsingle, 1);
+            single_list[slot] = t;
         } else {
-            int any = 0;
-            for (int u = s; u < e; ++u) any |= items[u].wanted;
-            if (any) {
-                int c = MRRR_ATOMIC_ADD(&C->ncluster, 1);
-                int m0 = MRRR_ATOMIC_ADD(&C->nmember, e - s);
-                unsigned long long off = MRRR_ATOMIC_ADD(&C->pool_need, 4ULL * (unsigned long long)items[s].n);
-                Cluster& K = clusters[c];
-                K.a = s;
-                K.b = e;
-                K.n = items[s].n;
-                K.pool_off = (long long)off;
-                K.gapL = gL;
-                K.gapR = gR;
-                K.depth = items[s].depth;
-                for (int u = s; u < e; ++u) {
-                    items[u].kind = KIND_CLUSTER;
-                    member_list[m0 + (u - s)] = u;
-                }
-                items[s].gapL = gL;
-                items[e - 1].gapR = gR;
-                MRRR_ATOMIC_MAX(&C->largest_cluster, e - s);
-                MRRR_ATOMIC_ADD(&C->nclusters_total, 1);
-            } else {
-                for (int u = s; u < e; ++u) items[u].kind = KIND_DROPPED;
-            }
+            I.kind = KIND_DROPPED;
         }
-        s = e;
+        return;
     }
+    int e = t + 1;
+    while (e + 1 <= K - 1 && same_group(items[e], items[e + 1]) && !separated(items[e], items[e + 1], gaptol)) ++e;
+    ++e;  // run [t, e)
+    bool has_e = e < K && same_group(items[e - 1], items[e]);
+    double gL = has_l ? I.lo - items[t - 1].hi : I.gapL;
+    double gR = has_e ? items[e].lo - items[e - 1].hi : items[e - 1].gapR;
+    int any = 0;
+    for (int u = t; u < e; ++u) any |= items[u].wanted;
+    if (!any) {
+        for (int u = t; u < e; ++u) items[u].kind = KIND_DROPPED;
+        return;
+    }
+    int c = MRRR_ATOMIC_ADD(&C->ncluster, 1);
+    int m0 = MRRR_ATOMIC_ADD(&C->nmember, e - t);
+    unsigned long long off = MRRR_ATOMIC_ADD(&C->pool_need, 4ULL * (unsigned long long)I.n);
+    Cluster& Kc = clusters[c];
+    Kc.a = t;
+    Kc.b = e;
+    Kc.n = I.n;
+    Kc.pool_off = (long long)off;
+    Kc.gapL = gL;
+    Kc.gapR = gR;
+    Kc.depth = I.depth;
+    for (int u = t; u < e; ++u) {
+        items[u].kind = KIND_CLUSTER;
+        member_list[m0 + (u - t)] = u;
+    }
+    items[t].gapL = gL;
+    items[e - 1].gapR = gR;
+    MRRR_ATOMIC_MAX(&C->largest_cluster, e - t);
+    MRRR_ATOMIC_ADD(&C->nclusters_total, 1);
 }
 
 // --------------------------------------------------------------- a5: cluster -> child rep
@@ -656,6 +672,20 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
 
 // --------------------------------------------------------------- a6 + a7: RQI and store
 
+// One twisted solve; on the device a binary64 solve with contiguous scratch
+// uses the tuned transform, which also reports the arg-max of |z| (else
+// *imax = -1).
+template <class Y>
+MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratch<Y>& Wk, Y* gamma, int* imax) {
+#if defined(__CUDA_ARCH__)
+    if constexpr (std::is_same<Y, double>::value) {
+        if (Wk.stride == 1) return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax);
+    }
+#endif
+    *imax = -1;
+    return twisted_solve<Y>(rep, n, lam, pm, Wk, gamma);
+}
+
 // Rayleigh quotient iteration with twisted factorizations, guarded by
 // bisection (Algorithm 1, line 10; Sec. 2, "Rayleigh quotient iteration"):
 // each step solves at lambda, updates the bracket with the inertia of the
@@ -688,6 +718,7 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     Y lam_out = lam;
     bool conv = false;
     int iters = 0;
+    int imax_t = -1;
     unsigned long long steps = 0;
     if (n == 1) {
         Wk.A(0) = from_d<Y>(1.0);
@@ -697,7 +728,7 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         conv = true;
     } else {
         for (int it = 0; it < cfg.max_rqi; ++it) {
-            tr = twisted_solve<Y>(rep, n, lam, pm, Wk, &gamma);
+            tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t);
             steps += 2ULL * n;
             ++iters;
             if (tr.neg >= I.j) hi = bmin(hi, lam);
@@ -720,7 +751,7 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
             rt = fmax(rt, 4.0 * cfg.eps_y);
             steps += bisect_bracket<Y, Y>(rep, n, I.j, lo, hi, B.pivmin, rt, 1, 600);
             lam = (lo + hi) * from_d<Y>(0.5);
-            tr = twisted_solve<Y>(rep, n, lam, pm, Wk, &gamma);
+            tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t);
             steps += 2ULL * n;
             ++iters;
             double nrm2 = to_d(tr.nrm2);
@@ -741,13 +772,16 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     double lam_T = (lt.hi + lt.lo) / M.scale;
     // normalise, fix the sign (largest entry positive), cast to x, store
     A_t nrm = ysqrt(tr.nrm2);
-    int imax = 0;
-    double zmax = -1.0;
-    for (int i = 0; i < n; ++i) {
-        double z = fabs(to_d(Wk.A(i)));
-        if (z > zmax) {
-            zmax = z;
-            imax = i;
+    int imax = imax_t;
+    if (imax < 0) {
+        imax = 0;
+        double zmax = -1.0;
+        for (int i = 0; i < n; ++i) {
+            double z = fabs(to_d(Wk.A(i)));
+            if (z > zmax) {
+                zmax = z;
+                imax = i;
+            }
         }
     }
     double sgn = to_d(Wk.A(imax)) < 0.0 ? -1.0 : 1.0;

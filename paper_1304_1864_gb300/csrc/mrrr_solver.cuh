@@ -27,13 +27,100 @@ template <class Y> struct LowOf { typedef float T; static constexpr bool use = f
 template <> struct LowOf<double> { typedef float T; static constexpr bool use = true; };
 template <> struct LowOf<dd> { typedef double T; static constexpr bool use = true; };
 
+// Preprocessing (Sec. 2 and Sec. 3.2, "Preprocessing"), one CTA per matrix:
+// ||T||_1 by a max-reduction, scaling by the power of two that brings it to
+// [1/2, 1), splitting where |e_i| <= eps_x ||T||_1, and the compact list of
+// blocks by a CTA-wide scan.  Same results as prep_matrix.
 template <class X>
 __global__ void k_prep(MatrixDesc* mats, BlockDesc* blocks, double* wd, double* we, SolveCfg cfg) {
-    int p = blockIdx.x;
-    if (threadIdx.x != 0) return;
-    MatrixDesc& M = mats[p];
-    prep_matrix<X>(M, blocks, wd, we, cfg);
-    for (int b = 0; b < M.nblocks; ++b) blocks[M.row0 + b].matrix = p;
+    constexpr int T = 256;
+    __shared__ double red[T];
+    __shared__ int cnt[T];
+    __shared__ int bad;
+    MatrixDesc& M = mats[blockIdx.x];
+    const int n = M.n;
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    double mx = 0.0;
+    for (int i = tid; i < n; i += T) {
+        double di = ld_x<X>(M.d, i);
+        double sum = fabs(di);
+        if (!isfinite(di)) bad = 1;
+        if (i > 0) sum += fabs(ld_x<X>(M.e, i - 1));
+        if (i < n - 1) {
+            double ei = ld_x<X>(M.e, i);
+            if (!isfinite(ei)) bad = 1;
+            sum += fabs(ei);
+        }
+        mx = fmax(mx, sum);
+    }
+    red[tid] = mx;
+    __syncthreads();
+    for (int w = T / 2; w > 0; w >>= 1) {
+        if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
+        __syncthreads();
+    }
+    const double tn = red[0];
+    if (bad || !isfinite(tn)) {
+        if (tid == 0) {
+            M.status = ST_ERR_NONFINITE;
+            M.nblocks = 0;
+        }
+        return;
+    }
+    double scale = 1.0;
+    if (tn > 0.0) {
+        int ex;
+        frexp(tn, &ex);
+        scale = ldexp(1.0, -ex);
+    }
+    const double thresh = cfg.eps_x * tn;
+    // rows [c0, c1) of this thread: scaled copy, split, block starts
+    const int per = (n + T - 1) / T;
+    const int c0 = min(n, tid * per), c1 = min(n, c0 + per);
+    int starts = 0;
+    for (int i = c0; i < c1; ++i) {
+        wd[M.row0 + i] = ld_x<X>(M.d, i) * scale;
+        if (i < n - 1) {
+            double ei = ld_x<X>(M.e, i);
+            we[M.row0 + i] = fabs(ei) <= thresh ? 0.0 : ei * scale;
+        } else {
+            we[M.row0 + i] = 0.0;
+        }
+        if (i == 0 || fabs(ld_x<X>(M.e, i - 1)) <= thresh) ++starts;
+    }
+    cnt[tid] = starts;
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int k = 0; k < T; ++k) {
+            int v = cnt[k];
+            cnt[k] = acc;
+            acc += v;
+        }
+        M.nblocks = acc;
+        M.scale = scale;
+        M.tnorm = tn;
+    }
+    __syncthreads();
+    int b = cnt[tid];
+    for (int i = c0; i < c1; ++i) {
+        if (i == 0 || fabs(ld_x<X>(M.e, i - 1)) <= thresh) {
+            BlockDesc& B = blocks[M.row0 + b];
+            B.matrix = blockIdx.x;
+            B.row0 = M.row0 + i;
+            B.mrow = i;
+            ++b;
+        }
+    }
+    __syncthreads();
+    const int nb = M.nblocks;
+    for (int k = tid; k < nb; k += T) {
+        BlockDesc& B = blocks[M.row0 + k];
+        int end = (k + 1 < nb) ? blocks[M.row0 + k + 1].mrow : n;
+        B.n = end - B.mrow;
+    }
 }
 
 // One CTA per block: the two candidate factorizations run on two warps, the
@@ -185,21 +272,13 @@ static __global__ void k_assign_cols(Item* items, int count, const MatrixDesc* m
     assign_col(t, items, mats, blocks);
 }
 
-static __global__ void k_classify_blocks(const int* blist, int nb, const BlockDesc* blocks, Item* items,
-                                         double gaptol, int* single_list, Cluster* clusters, int* member_list,
-                                         DevCounters* C) {
+// One thread per item of the list (all items at the root level, the members
+// of the previous level's clusters below it).
+static __global__ void k_classify(Item* items, const int* list, int count, int K, double gaptol, int* single_list,
+                                  Cluster* clusters, int* member_list, DevCounters* C) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nb) return;
-    const BlockDesc& B = blocks[blist[t]];
-    if (B.nitems == 0) return;
-    classify_group(B.item0, B.item0 + B.nitems, items, gaptol, single_list, clusters, member_list, C);
-}
-
-static __global__ void k_classify_clusters(const Cluster* groups, int ng, Item* items, double gaptol,
-                                           int* single_list, Cluster* clusters, int* member_list, DevCounters* C) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ng) return;
-    classify_group(groups[t].a, groups[t].b, items, gaptol, single_list, clusters, member_list, C);
+    if (t >= count) return;
+    classify_item(list ? list[t] : t, items, K, gaptol, single_list, clusters, member_list, C);
 }
 
 template <class Y, class Lo>
@@ -216,11 +295,12 @@ __global__ void k_rqi(Item* items, const int* list, int count, MatrixDesc* mats,
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
     Item& I = items[list[t]];
+    // each eigenpair owns two contiguous arrays of nmax words
     Scratch<Y> Wk;
-    Y* base = scratch + (size_t)(t >> 5) * (size_t)(2 * nmax) * 32 + (t & 31);
+    Y* base = scratch + (size_t)t * (size_t)(2 * nmax);
     Wk.a = base;
-    Wk.b = base + (size_t)nmax * 32;
-    Wk.stride = 32;
+    Wk.b = base + nmax;
+    Wk.stride = 1;
     rqi_item<X, Y>(I, mats, blocks, cfg, Wk, C);
 }
 
@@ -378,7 +458,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
 
     // a1: scale + split
     tl.begin(MRRR_PHASE_PREP);
-    k_prep<X><<<P, 32, 0, st>>>(d_mats, d_blocks, wd, we, cfg);
+    k_prep<X><<<P, 256, 0, st>>>(d_mats, d_blocks, wd, we, cfg);
     tl.end();
     MRRR_CK(cudaGetLastError());
     MRRR_CK(cudaMemcpyAsync(mats, d_mats, sizeof(MatrixDesc) * P, cudaMemcpyDeviceToHost, st));
@@ -404,7 +484,8 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         if (K > 0) {
             MRRR_ALLOC(items, Item, K);
             MRRR_ALLOC(single_list, int, K);
-            MRRR_ALLOC(member_list, int, K);
+            MRRR_ALLOC(member_a, int, K);
+            MRRR_ALLOC(member_b, int, K);
             MRRR_ALLOC(refine_list, int, K);
             MRRR_ALLOC(clus_a, Cluster, K / 2 + 1);
             MRRR_ALLOC(clus_b, Cluster, K / 2 + 1);
@@ -472,22 +553,19 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             // a4/a5: classification and the representation tree, level by level;
             // the singletons of the root level go to a second stream so their
             // RQI overlaps the (latency-bound) cluster levels
-            Cluster* groups = nullptr;
-            int ngroups = 0;
+            const int* prev_members = nullptr;
+            int nprev = K;
             int s_root = -1;
             for (int level = 0;; ++level) {
                 Cluster* out = (level % 2 == 0) ? clus_a : clus_b;
+                int* members = (level % 2 == 0) ? member_a : member_b;
                 MRRR_CK(cudaMemsetAsync(&d_C->pool_need, 0, sizeof(unsigned long long), st));
                 MRRR_CK(cudaMemsetAsync(&d_C->ncluster, 0, 2 * sizeof(int), st));  // ncluster, nmember
                 bool force = level >= max_depth;
                 double gt = force ? -INFINITY : cfg.gaptol;
                 tl.begin(MRRR_PHASE_CLASSIFY);
-                if (level == 0)
-                    k_classify_blocks<<<grid_for(NB), kThreads, 0, st>>>(d_blist, NB, d_blocks, items, gt,
-                                                                         single_list, out, member_list, d_C);
-                else
-                    k_classify_clusters<<<grid_for(ngroups), kThreads, 0, st>>>(groups, ngroups, items, gt,
-                                                                                single_list, out, member_list, d_C);
+                k_classify<<<grid_for(nprev), kThreads, 0, st>>>(items, prev_members, nprev, K, gt, single_list, out,
+                                                                 members, d_C);
                 tl.end();
                 MRRR_CK(cudaGetLastError());
                 MRRR_CK(cudaMemcpyAsync(&C, d_C, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
@@ -510,10 +588,9 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                                                                           pool_lo, cfg, d_C);
                 tl.end();
                 MRRR_CK(cudaGetLastError());
-                if (approximate(member_list, C.nmember, true, &d_C->qd_refine, MRRR_PHASE_REFINE))
-                    return MRRR_ERR_CUDA;
-                groups = out;
-                ngroups = C.ncluster;
+                if (approximate(members, C.nmember, true, &d_C->qd_refine, MRRR_PHASE_REFINE)) return MRRR_ERR_CUDA;
+                prev_members = members;
+                nprev = C.nmember;
             }
             // a6/a7: RQI for the remaining singletons
             {
