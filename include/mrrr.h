@@ -151,6 +151,47 @@ int mrrr_solve_batch_d(int nb, const int* n, const double* const* d, const doubl
                        const int* iu, mrrr_mode mode, const mrrr_params* params, int* m_out, double* const* W,
                        double* const* Z, const int* ldz, int* status, void* stream);
 
+/*
+ * Eigenvectors for given eigenvalues without any device allocation.
+ *
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory at the point of the call -- code running
+ * while a CUDA graph is being captured, real-time or embedded hosts that fix
+ * their memory at start-up, or libraries whose device memory is owned by
+ * another framework's allocator.  It runs the solver's Rayleigh-quotient /
+ * twisted-factorization kernel on one fixed scratch array instead of
+ * allocated buffers, and calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *
+ * Input: T (d[0..n-1], e[0..n-2], binary32, device pointers) and k of its
+ * eigenvalues W[0..k-1] = lambda_il .. lambda_{il+k-1} in ascending order
+ * (for instance as returned by mrrr_solve_s).  Output: Z (device, n x k,
+ * column-major, leading dimension ldz >= n), column t the unit eigenvector of
+ * lambda_{il+t}, largest entry positive.  Work: root representation with
+ * binary64 internals as in mrrr_solve_s (MRRR_MIXED), each given eigenvalue
+ * bracketed by binary64 Sturm counts, then the RQI of Algorithm 1, line 10,
+ * on that one representation -- no representation tree, so eigenvalues must
+ * be separated relative to each other by more than 1e-5 (the mixed gaptol);
+ * within tighter clusters use mrrr_solve_s.  The matrix must not split (no
+ * |e_i| <= 2^-24 ||T||_1).
+ *
+ * Limits: n <= MRRR_NOALLOC_MAX_N and k <= MRRR_NOALLOC_MAX_K; larger sizes,
+ * host pointers and reducible matrices return MRRR_ERR_ARG (nothing is
+ * launched).  The scratch is one file-scope device array of
+ * MRRR_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current, so make
+ * that first call before any stream capture begins.  All calls share the
+ * array and it keeps the previous call's contents; calls whose work overlaps
+ * on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  The call returns when the results are complete on `stream`.
+ */
+#define MRRR_NOALLOC_MAX_N 1024
+#define MRRR_NOALLOC_MAX_K 1024
+#define MRRR_NOALLOC_SCRATCH_BYTES 16839680
+int mrrr_eigvecs_noalloc_s(int n, const float* d, const float* e, int il, int k, const float* W, float* Z,
+                           int ldz, void* stream);
+
 /* Human-readable text for a status code (static storage). */
 const char* mrrr_strerror(int status);
 

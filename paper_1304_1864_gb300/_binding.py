@@ -69,6 +69,9 @@ def lib():
             f.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_int, ctypes.POINTER(MrrrParams), vp,
                           vp, vp, vp, vp, vp]
             f.restype = ctypes.c_int
+        L.mrrr_eigvecs_noalloc_s.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
+                                             vp]
+        L.mrrr_eigvecs_noalloc_s.restype = ctypes.c_int
         L.mrrr_strerror.argtypes = [ctypes.c_int]
         L.mrrr_strerror.restype = ctypes.c_char_p
         L.mrrr_version.argtypes = []
@@ -100,6 +103,10 @@ def mrrr_solve_batch_s(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, stat
 
 def mrrr_solve_batch_d(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, status, stream):
     return lib().mrrr_solve_batch_d(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, status, stream)
+
+
+def mrrr_eigvecs_noalloc_s(n, d, e, il, k, W, Z, ldz, stream):
+    return lib().mrrr_eigvecs_noalloc_s(n, d, e, il, k, W, Z, ldz, stream)
 
 
 def mrrr_strerror(code):

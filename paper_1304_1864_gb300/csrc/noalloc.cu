@@ -1,0 +1,231 @@
+// Eigenvectors for given eigenvalues with no device allocation at all: a
+// variant of the RQI kernel whose scratch lives in one file-scope device array
+// (see mrrr_eigvecs_noalloc_s in include/mrrr.h).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "mrrr.h"
+#include "mrrr_phases.cuh"
+
+namespace {
+
+using namespace mrrr;
+
+constexpr int kMaxN = MRRR_NOALLOC_MAX_N;
+constexpr int kMaxK = MRRR_NOALLOC_MAX_K;
+
+// Layout of the static scratch (byte offsets, each 256-aligned).
+constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kOffMat = 0;
+constexpr size_t kOffBlk = align256(kOffMat + sizeof(MatrixDesc));
+constexpr size_t kOffCnt = align256(kOffBlk + sizeof(BlockDesc));
+constexpr size_t kOffStatus = align256(kOffCnt + sizeof(DevCounters));
+constexpr size_t kOffWd = align256(kOffStatus + sizeof(int));
+constexpr size_t kOffWe = align256(kOffWd + sizeof(double) * kMaxN);
+constexpr size_t kOffRep = align256(kOffWe + sizeof(double) * kMaxN);
+constexpr size_t kOffRepLo = align256(kOffRep + sizeof(double) * 4 * kMaxN);
+constexpr size_t kOffWout = align256(kOffRepLo + sizeof(float) * 2 * kMaxN);
+constexpr size_t kOffWork = align256(kOffWout + sizeof(float) * kMaxK);
+constexpr size_t kBytes = align256(kOffWork + sizeof(double) * 2 * (size_t)kMaxN * kMaxK);
+static_assert(kBytes == MRRR_NOALLOC_SCRATCH_BYTES, "header constant must match the layout");
+
+// The scratch array.  In host code this name is only a stand-in for the
+// symbol: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_scratch[kBytes];
+
+enum : int { NA_OK = 0, NA_NONFINITE = 1, NA_REDUCIBLE = 2 };
+
+// Kernel 1 (one CTA): scale, check irreducibility, root representation.
+__global__ void k_noalloc_root(unsigned char* base, const float* d, const float* e, int n, SolveCfg cfg) {
+    MatrixDesc& M = *(MatrixDesc*)(base + kOffMat);
+    BlockDesc& B = *(BlockDesc*)(base + kOffBlk);
+    int* status = (int*)(base + kOffStatus);
+    double* wd = (double*)(base + kOffWd);
+    double* we = (double*)(base + kOffWe);
+    double* rep = (double*)(base + kOffRep);
+    float* rep_lo = (float*)(base + kOffRepLo);
+    __shared__ double s_gl, s_gu, s_g[2], s_mu[2];
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) {
+        double tn = 0.0;
+        int bad = NA_OK;
+        for (int i = 0; i < n; ++i) {
+            double s = fabs((double)d[i]);
+            if (!isfinite((double)d[i])) bad = NA_NONFINITE;
+            if (i > 0) s += fabs((double)e[i - 1]);
+            if (i < n - 1) {
+                if (!isfinite((double)e[i])) bad = NA_NONFINITE;
+                s += fabs((double)e[i]);
+            }
+            tn = fmax(tn, s);
+        }
+        double scale = 1.0;
+        if (tn > 0.0) {
+            int ex;
+            frexp(tn, &ex);
+            scale = ldexp(1.0, -ex);
+        }
+        for (int i = 0; i < n; ++i) {
+            wd[i] = (double)d[i] * scale;
+            we[i] = i < n - 1 ? (double)e[i] * scale : 0.0;
+            if (bad == NA_OK && i < n - 1 && fabs((double)e[i]) <= cfg.eps_x * tn) bad = NA_REDUCIBLE;
+        }
+        memset(&M, 0, sizeof(M));
+        M.n = n;
+        M.nblocks = 1;
+        M.scale = scale;
+        M.tnorm = tn;
+        M.range = RANGE_ALL;
+        memset(&B, 0, sizeof(B));
+        B.matrix = 0;
+        B.row0 = 0;
+        B.mrow = 0;
+        B.n = n;
+        *status = bad;
+        s_bad = bad;
+        if (bad == NA_OK) root_bounds<double>(B, wd, we, &s_gl, &s_gu);
+    }
+    __syncthreads();
+    if (s_bad != NA_OK) return;
+    if (n == 1) {
+        if (threadIdx.x == 0) root_trivial<double, float>(B, wd, rep, rep_lo);
+        return;
+    }
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+        int side = threadIdx.x == 32;
+        s_g[side] = root_candidate<double>(B, wd, we, rep, s_gl, s_gu, side, &s_mu[side]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) root_choose(B, M, s_gl, s_gu, s_g[0], s_mu[0], s_g[1], s_mu[1], cfg);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) root_move<double>(B, rep, i);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) root_element<double, float>(B, M, rep, rep_lo, i, cfg);
+}
+
+// Kernel 2 (one thread per eigenvalue): bracket the given eigenvalue
+// lambda_{il+t} in the root rep, then the RQI of the solver (twisted
+// factorizations, guarded by bisection) with its scratch in the static array.
+__global__ void k_noalloc_rqi(unsigned char* base, const float* W, int il, int k, float* Z, int ldz, SolveCfg cfg) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= k) return;
+    if (*(const int*)(base + kOffStatus) != NA_OK) return;
+    MatrixDesc* mats = (MatrixDesc*)(base + kOffMat);
+    const BlockDesc* blocks = (const BlockDesc*)(base + kOffBlk);
+    DevCounters* C = (DevCounters*)(base + kOffCnt);
+    const BlockDesc& B = blocks[0];
+    MatrixDesc M = mats[0];  // private copy: outputs of this call
+    M.W = base + kOffWout;
+    M.Z = Z;
+    M.ldz = ldz;
+    const int n = M.n;
+    double lam = (double)W[t] * M.scale - B.mu;
+    double w = 4.0 * cfg.eps_x * (fabs((double)W[t]) * M.scale + fabs(B.mu)) + 4.0 * B.pivmin;
+    Item I;
+    memset(&I, 0, sizeof(I));
+    I.lo = lam - w;
+    I.hi = lam + w;
+    I.rep = base + kOffRep;
+    I.rep_lo = base + kOffRepLo;
+    I.n = n;
+    I.j = il + t;
+    I.block = 0;
+    I.matrix = 0;
+    I.outcol = t;
+    I.sig_hi = B.mu;
+    I.wanted = 1;
+    int fails = 0;
+    verify_endpoint<double>(I, B, 0, &fails);
+    verify_endpoint<double>(I, B, 1, &fails);
+    // gaps from the neighbouring given eigenvalues (one side open at the ends)
+    I.gapL = t > 0 ? fmax(lam - ((double)W[t - 1] * M.scale - B.mu) - w, 0.5 * w) : INFINITY;
+    I.gapR = t + 1 < k ? fmax(((double)W[t + 1] * M.scale - B.mu) - lam - w, 0.5 * w) : INFINITY;
+    Scratch<double> Wk;
+    Wk.a = (double*)(base + kOffWork) + (size_t)t * 2 * kMaxN;
+    Wk.b = Wk.a + kMaxN;
+    Wk.stride = 1;
+    rqi_item<float, double>(I, &M, blocks, cfg, Wk, C);
+}
+
+// Device address of the scratch array, looked up once per device with that
+// device current.
+std::mutex g_mu;
+void* g_addr[64];
+bool g_done[64];
+
+int scratch_address(unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return MRRR_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_done[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return MRRR_ERR_CUDA;
+        }
+        g_addr[dev] = p;
+        g_done[dev] = true;
+    }
+    *out = (unsigned char*)g_addr[dev];
+    return MRRR_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int mrrr_eigvecs_noalloc_s(int n, const float* d, const float* e, int il, int k, const float* W,
+                                      float* Z, int ldz, void* stream) {
+    if (n < 1 || n > MRRR_NOALLOC_MAX_N || k < 1 || k > MRRR_NOALLOC_MAX_K) return MRRR_ERR_ARG;
+    if (il < 1 || il + k - 1 > n || ldz < n) return MRRR_ERR_ARG;
+    if (!d || (n > 1 && !e) || !W || !Z) return MRRR_ERR_ARG;
+    int devs = 0;
+    if (cudaGetDeviceCount(&devs) != cudaSuccess || devs == 0) {
+        cudaGetLastError();
+        return MRRR_ERR_CUDA;
+    }
+    if (!is_device_ptr(d) || (n > 1 && !is_device_ptr(e)) || !is_device_ptr(W) || !is_device_ptr(Z))
+        return MRRR_ERR_ARG;
+    unsigned char* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc != MRRR_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveCfg cfg;
+    cfg.eps_x = 5.9604644775390625e-08;
+    cfg.eps_y = 1.1102230246251565e-16;
+    cfg.mixed = 1;
+    cfg.gaptol = 1e-5;
+    cfg.rtol_class = 1e-7;
+    cfg.xi = 4.0 * cfg.eps_x;
+    cfg.krs = 1.0;
+    cfg.growth_k = 8.0;
+    cfg.max_rqi = 10;
+    cfg.seed = 0;
+    cfg.flags = 0;
+    // the counters of the previous call must not leak into this one
+    if (cudaMemsetAsync(base + kOffCnt, 0, sizeof(DevCounters), st) != cudaSuccess) return MRRR_ERR_CUDA;
+    k_noalloc_root<<<1, 64, 0, st>>>(base, d, n > 1 ? e : d, n, cfg);
+    k_noalloc_rqi<<<(k + 63) / 64, 64, 0, st>>>(base, W, il, k, Z, ldz, cfg);
+    if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
+    int status = 0;
+    DevCounters C;
+    if (cudaMemcpyAsync(&status, base + kOffStatus, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&C, base + kOffCnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return MRRR_ERR_CUDA;
+    if (status == NA_NONFINITE) return MRRR_ERR_NONFINITE;
+    if (status == NA_REDUCIBLE) return MRRR_ERR_ARG;
+    return C.noconv > 0 ? MRRR_ERR_NOCONV : MRRR_OK;
+}
