@@ -29,6 +29,9 @@ __device__ __forceinline__ unsigned long long dabsbits(double x) {
 }
 __device__ __forceinline__ bool dfinite(double x) { return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u; }
 
+// rows per software-prefetch group for the per-eigenpair scratch arrays
+constexpr int kG = 8;
+
 // reciprocal estimate refined by `steps` Newton-Raphson iterations
 template <int steps>
 __device__ __forceinline__ double drcp(double b) {
@@ -67,71 +70,198 @@ __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const
     return cnt;
 }
 
+// Stationary transform on rows [0, m): l+_i -> A[i] and, if B != nullptr,
+// s_i -> B[i].  Returns s_m; *neg += number of negative d+_i, i < m.
+__device__ __forceinline__ double stationary_fast(const double* __restrict__ D, const double* __restrict__ L,
+                                                  const double* __restrict__ LD, int m, double lam,
+                                                  double* __restrict__ A, double* __restrict__ B, int* neg) {
+    double s = -lam;
+    if (m <= 0) return s;
+    int c = 0;
+    double dn = __ldg(D), ldn = __ldg(LD), lnx = __ldg(L);
+    for (int i = 0; i < m; ++i) {
+        double di = dn, ldi = ldn, li = lnx;
+        dn = __ldg(D + i + 1);
+        ldn = __ldg(LD + i + 1);
+        lnx = __ldg(L + i + 1);
+        double dp = di + s;
+        c += dsign(dp);
+        double lp = ldi * drcp<2>(dp);
+        A[i] = lp;
+        if (B) B[i] = s;
+        s = fma(lp * li, s, -lam);
+    }
+    *neg += c;
+    return s;
+}
+
+// N_r^T z = e_r from l+ (A, rows < r) and u (B, rows >= r); z overwrites A.
+// Every lane runs n-1 steps -- first r steps downward from r (z_i = -l+_i
+// z_{i+1}), then n-1-r steps upward (z_{i+1} = -u_i z_i) -- so lanes with
+// different r do not diverge; the coefficient of the next step is loaded
+// one step ahead.  Returns ||z||^2; *imax = index of the largest |z_i|
+// (smallest index on ties).
+__device__ __forceinline__ double solve_twisted_fast(const double* __restrict__ LD, int n, int r,
+                                                     double* __restrict__ A, const double* __restrict__ B,
+                                                     int* imax) {
+    double nrm2 = 1.0;
+    A[r] = 1.0;
+    unsigned long long zmax = dabsbits(1.0);
+    int im = r;
+    double zprev = 1.0;   // z at the previous position of the walk
+    double zprev2 = 0.0;  // z two positions back (for the zero rule)
+    // coefficient of walk step k: l+_{r-1-k} downward, u_k upward; loaded a
+    // group of kG steps ahead
+    double cur[kG], nxt[kG];
+#pragma unroll
+    for (int k = 0; k < kG; ++k) cur[k] = k < n - 1 ? (k < r ? A[r - 1 - k] : B[k]) : 0.0;
+    for (int k0 = 0; k0 < n - 1; k0 += kG) {
+#pragma unroll
+        for (int q = 0; q < kG; ++q) {
+            int kk = k0 + kG + q;
+            nxt[q] = kk < n - 1 ? (kk < r ? A[r - 1 - kk] : B[kk]) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kG; ++q) {
+            int k = k0 + q;
+            if (k < n - 1) {
+                int i;
+                bool down = k < r;
+                if (down) {
+                    i = r - 1 - k;
+                } else {
+                    i = k + 1;
+                    if (k == r) {  // the upward walk restarts at z_r = 1
+                        zprev = 1.0;
+                        zprev2 = 0.0;
+                    }
+                }
+                double z;
+                if (dabsbits(zprev) != 0) {
+                    z = -(cur[q] * zprev);
+                } else if (down) {
+                    // row i+1 with z_{i+1} = 0: e_i z_i + e_{i+1} z_{i+2} = 0
+                    z = (i + 2 < n) ? -(__ldg(LD + i + 1) / __ldg(LD + i)) * zprev2 : 0.0;
+                } else {
+                    // row i-1 with z_{i-1} = 0: e_{i-2} z_{i-2} + e_{i-1} z_i = 0
+                    z = (i >= 2) ? -(__ldg(LD + i - 2) / __ldg(LD + i - 1)) * zprev2 : 0.0;
+                }
+                A[i] = z;
+                nrm2 = fma(z, z, nrm2);
+                unsigned long long za = dabsbits(z);
+                if (za > zmax || (za == zmax && i < im)) {
+                    zmax = za;
+                    im = i;
+                }
+                zprev2 = zprev;
+                zprev = z;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kG; ++q) cur[q] = nxt[q];
+    }
+    *imax = im;
+    return nrm2;
+}
+
 // One twisted-factorization solve at lam for an eigenpair whose scratch
 // arrays A, B (n words each) are contiguous; same results contract as
 // twisted_solve: z in A (z_r = 1), returns r, inertia count and ||z||^2;
 // *imax receives the index of the entry of largest magnitude.
+//
+// r_fixed < 0: the full factorization -- stationary transform top-down,
+// progressive transform bottom-up, r = argmin |gamma_k| (Sec. 2, RQI steps
+// (i)-(ii)).  r_fixed >= 0: the twist index is given (the largest entry of
+// the previous iterate, as e_r then has a large component along the wanted
+// eigenvector), and only rows < r of the stationary and rows > r of the
+// progressive transform are needed -- one pass instead of two.  In both
+// cases the inertia of Delta_r = diag(d+_0..d+_{r-1}, gamma_r,
+// w_{r+1}..w_{n-1}) is the Sturm count at lam (Sylvester), used to update
+// the bisection bracket.
 __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* __restrict__ rep, int n, double lam,
                                                                  double pivmin, double* __restrict__ A,
-                                                                 double* __restrict__ B, double* gamma,
-                                                                 int* imax) {
+                                                                 double* __restrict__ B, double* gamma, int* imax,
+                                                                 int r_fixed = -1) {
     const double* __restrict__ D = rep;
     const double* __restrict__ L = rep + n;
     const double* __restrict__ LD = rep + 2 * n;
     const double* __restrict__ LLD = rep + 3 * n;
     TwistResult<double> res;
-    // stationary transform, top-down: l+_i -> A, s_i -> B
-    double s = -lam;
     int neg = 0;
-    bool bad = false;
-    {
-        double dn = __ldg(D), ldn = __ldg(LD), lnx = __ldg(L);
-        for (int i = 0; i < n - 1; ++i) {
-            double di = dn, ldi = ldn, li = lnx;
-            dn = __ldg(D + i + 1);
-            ldn = __ldg(LD + i + 1);
-            lnx = __ldg(L + i + 1);
-            double dp = di + s;
-            neg += dsign(dp);
-            double lp = ldi * drcp<2>(dp);
-            A[i] = lp;
-            B[i] = s;
-            s = fma(lp * li, s, -lam);
-        }
-        double dp = dn + s;
-        neg += dsign(dp);
-        bad = !dfinite(s) || !dfinite(dp);
-    }
-    // progressive transform, bottom-up: gamma_k, u_k -> B
-    double p = __ldg(D + n - 1) - lam;
-    double gbest = s + p + lam;
-    int r = n - 1;
-    unsigned long long gb = dabsbits(gbest);
-    {
-        double lldn = n > 1 ? __ldg(LLD + n - 2) : 0.0, dn = n > 1 ? __ldg(D + n - 2) : 0.0;
-        double lnx = n > 1 ? __ldg(L + n - 2) : 0.0, bn = n > 1 ? B[n - 2] : 0.0;
-        for (int i = n - 2; i >= 0; --i) {
-            double lldi = lldn, di = dn, li = lnx, si = bn;
-            if (i > 0) {
-                lldn = __ldg(LLD + i - 1);
-                dn = __ldg(D + i - 1);
-                lnx = __ldg(L + i - 1);
-                bn = B[i - 1];
+    int r;
+    double gbest;
+    bool bad;
+    if (r_fixed < 0) {
+        // stationary transform, top-down: l+_i -> A, s_i -> B
+        double s = stationary_fast(D, L, LD, n - 1, lam, A, B, &neg);
+        double dlast = __ldg(D + n - 1) + s;
+        neg += dsign(dlast);
+        bad = !dfinite(s) || !dfinite(dlast);
+        // progressive transform, bottom-up: gamma_k, u_k -> B
+        double p = __ldg(D + n - 1) - lam;
+        gbest = s + p + lam;
+        r = n - 1;
+        unsigned long long gb = dabsbits(gbest);
+        // rows n-2 .. 0 in groups of kG; the s_i of the next group (per-lane
+        // scratch, usually not in L1) are loaded a whole group ahead
+        double cur[kG], nxt[kG];
+#pragma unroll
+        for (int k = 0; k < kG; ++k) cur[k] = (n - 2 - k >= 0) ? B[n - 2 - k] : 0.0;
+        for (int i0 = n - 2; i0 >= 0; i0 -= kG) {
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                int ii = i0 - kG - k;
+                nxt[k] = ii >= 0 ? B[ii] : 0.0;
             }
-            double om = lldi + p;
-            double t = di * drcp<2>(om);
-            double um = li * t;
-            p = fma(p, t, -lam);
-            double g = (si + p) + lam;
-            B[i] = um;
-            unsigned long long ga = dabsbits(g);
-            if (ga <= gb) {  // smallest index on ties
-                gb = ga;
-                gbest = g;
-                r = i;
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                int i = i0 - k;
+                if (i >= 0) {
+                    double om = __ldg(LLD + i) + p;
+                    double t = __ldg(D + i) * drcp<2>(om);
+                    double um = __ldg(L + i) * t;
+                    p = fma(p, t, -lam);
+                    double g = (cur[k] + p) + lam;
+                    B[i] = um;
+                    unsigned long long ga = dabsbits(g);
+                    if (ga <= gb) {  // smallest index on ties
+                        gb = ga;
+                        gbest = g;
+                        r = i;
+                    }
+                }
             }
+#pragma unroll
+            for (int k = 0; k < kG; ++k) cur[k] = nxt[k];
         }
         bad = bad || !dfinite(p);
+    } else {
+        r = r_fixed;
+        // rows < r of the stationary transform (l+ -> A, no s needed)
+        double s = stationary_fast(D, L, LD, r, lam, A, nullptr, &neg);
+        // rows > r of the progressive transform (u -> B), counting w_{i+1} < 0
+        double p = __ldg(D + n - 1) - lam;
+        int c = 0;
+        if (r < n - 1) {
+            double lldn = __ldg(LLD + n - 2), dn = __ldg(D + n - 2), lnx = __ldg(L + n - 2);
+            for (int i = n - 2; i >= r; --i) {
+                double lldi = lldn, di = dn, li = lnx;
+                if (i > r) {
+                    lldn = __ldg(LLD + i - 1);
+                    dn = __ldg(D + i - 1);
+                    lnx = __ldg(L + i - 1);
+                }
+                double om = lldi + p;
+                c += dsign(om);
+                double t = di * drcp<2>(om);
+                B[i] = li * t;
+                p = fma(p, t, -lam);
+            }
+        }
+        neg += c;
+        gbest = s + p + lam;
+        neg += dsign(gbest);
+        bad = !dfinite(s) || !dfinite(p) || !dfinite(gbest);
     }
     if (bad) {
         // a pivot vanished: redo with the guarded generic transform
@@ -152,55 +282,9 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
         *imax = im;
         return res;
     }
-    // N_r^T z = e_r: every lane runs n-1 steps -- first r steps downward from
-    // r (z_i = -l+_i z_{i+1}), then n-1-r steps upward (z_{i+1} = -u_i z_i)
-    // -- so lanes with different r do not diverge.  The coefficient of the
-    // next step is loaded one step ahead.
-    double nrm2 = 1.0;
-    A[r] = 1.0;
-    unsigned long long zmax = dabsbits(1.0);
-    int im = r;
-    double zprev = 1.0;   // z at the previous position of the walk
-    double zprev2 = 0.0;  // z two positions back (for the zero rule)
-    double cn = n > 1 ? (0 < r ? A[r - 1] : B[0]) : 0.0;
-    for (int k = 0; k < n - 1; ++k) {
-        double c = cn;
-        if (k + 1 < n - 1) cn = (k + 1 < r) ? A[r - 2 - k] : B[k + 1];
-        int i;
-        bool down = k < r;
-        if (down) {
-            i = r - 1 - k;
-        } else {
-            i = k + 1;
-            if (k == r) {  // the upward walk restarts at z_r = 1
-                zprev = 1.0;
-                zprev2 = 0.0;
-            }
-        }
-        double z;
-        if (dabsbits(zprev) != 0) {
-            z = -(c * zprev);
-        } else if (down) {
-            // row i+1 with z_{i+1} = 0: e_i z_i + e_{i+1} z_{i+2} = 0
-            z = (i + 2 < n) ? -(__ldg(LD + i + 1) / __ldg(LD + i)) * zprev2 : 0.0;
-        } else {
-            // row i-1 with z_{i-1} = 0: e_{i-2} z_{i-2} + e_{i-1} z_i = 0
-            z = (i >= 2) ? -(__ldg(LD + i - 2) / __ldg(LD + i - 1)) * zprev2 : 0.0;
-        }
-        A[i] = z;
-        nrm2 = fma(z, z, nrm2);
-        unsigned long long za = dabsbits(z);
-        if (za > zmax || (za == zmax && i < im)) {
-            zmax = za;
-            im = i;
-        }
-        zprev2 = zprev;
-        zprev = z;
-    }
-    *imax = im;
+    res.nrm2 = solve_twisted_fast(LD, n, r, A, B, imax);
     res.r = r;
     res.neg = neg;
-    res.nrm2 = nrm2;
     *gamma = gbest;
     return res;
 }

@@ -674,14 +674,16 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
 
 // One twisted solve; on the device a binary64 solve with contiguous scratch
 // uses the tuned transform, which also reports the arg-max of |z| (else
-// *imax = -1).
+// *imax = -1) and can reuse a given twist index r_hint >= 0.
 template <class Y>
-MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratch<Y>& Wk, Y* gamma, int* imax) {
+MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratch<Y>& Wk, Y* gamma, int* imax,
+                                  int r_hint) {
 #if defined(__CUDA_ARCH__)
     if constexpr (std::is_same<Y, double>::value) {
-        if (Wk.stride == 1) return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax);
+        if (Wk.stride == 1) return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax, r_hint);
     }
 #endif
+    (void)r_hint;
     *imax = -1;
     return twisted_solve<Y>(rep, n, lam, pm, Wk, gamma);
 }
@@ -727,9 +729,13 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         lam_out = from_d<Y>(0.0);
         conv = true;
     } else {
+        // after the first step the twist index is the largest entry of the
+        // previous iterate (one pass of the transforms instead of two)
+        int r_hint = -1;
         for (int it = 0; it < cfg.max_rqi; ++it) {
-            tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t);
-            steps += 2ULL * n;
+            tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t, r_hint);
+            steps += (r_hint < 0 ? 2ULL : 1ULL) * n;
+            r_hint = imax_t;
             ++iters;
             if (tr.neg >= I.j) hi = bmin(hi, lam);
             else lo = bmax(lo, lam);
@@ -751,7 +757,7 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
             rt = fmax(rt, 4.0 * cfg.eps_y);
             steps += bisect_bracket<Y, Y>(rep, n, I.j, lo, hi, B.pivmin, rt, 1, 600);
             lam = (lo + hi) * from_d<Y>(0.5);
-            tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t);
+            tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t, -1);
             steps += 2ULL * n;
             ++iters;
             double nrm2 = to_d(tr.nrm2);
