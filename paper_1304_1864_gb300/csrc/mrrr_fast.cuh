@@ -51,22 +51,42 @@ __device__ __forceinline__ double drcp(double b) {
 // units of 2^-46, far inside what classification needs (relative accuracy
 // 1e-2 gaptol >= 1e-12).  The loop runs unguarded; if a pivot vanished the
 // recurrence produces a non-finite value and the guarded count is used.
+// Guarded fallbacks, kept out of line so that they do not weigh on the
+// register allocation and scheduling of the unguarded hot loops.
+static __device__ __noinline__ int negcount_guarded(const double* D, const double* LLD, int n, double tau, double pivmin) {
+    return negcount<double>(D, LLD, n, tau, pivmin);
+}
+
 __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const double* __restrict__ LLD, int n,
                                              double tau, double pivmin) {
     double s = -tau;
     int cnt = 0;
-    double dn = __ldg(D), ln = __ldg(LLD);
-    for (int i = 0; i < n - 1; ++i) {
-        double di = dn, li = ln;
-        dn = __ldg(D + i + 1);
-        ln = __ldg(LLD + i + 1);
-        double dp = di + s;
+    int i = 0;
+    // four rows per iteration with their loads issued together
+    for (; i + 4 <= n - 1; i += 4) {
+        double d0 = __ldg(D + i), d1 = __ldg(D + i + 1), d2 = __ldg(D + i + 2), d3 = __ldg(D + i + 3);
+        double l0 = __ldg(LLD + i), l1 = __ldg(LLD + i + 1), l2 = __ldg(LLD + i + 2), l3 = __ldg(LLD + i + 3);
+        double dp = d0 + s;
         cnt += dsign(dp);
-        s = fma(s * li, drcp<1>(dp), -tau);
+        s = fma(s * l0, drcp<1>(dp), -tau);
+        dp = d1 + s;
+        cnt += dsign(dp);
+        s = fma(s * l1, drcp<1>(dp), -tau);
+        dp = d2 + s;
+        cnt += dsign(dp);
+        s = fma(s * l2, drcp<1>(dp), -tau);
+        dp = d3 + s;
+        cnt += dsign(dp);
+        s = fma(s * l3, drcp<1>(dp), -tau);
     }
-    double dp = dn + s;
+    for (; i < n - 1; ++i) {
+        double dp = __ldg(D + i) + s;
+        cnt += dsign(dp);
+        s = fma(s * __ldg(LLD + i), drcp<1>(dp), -tau);
+    }
+    double dp = __ldg(D + n - 1) + s;
     cnt += dsign(dp);
-    if (!dfinite(s) || !dfinite(dp)) return negcount<double>(D, LLD, n, tau, pivmin);
+    if (!dfinite(s) || !dfinite(dp)) return negcount_guarded(D, LLD, n, tau, pivmin);
     return cnt;
 }
 
@@ -93,6 +113,68 @@ __device__ __forceinline__ double stationary_fast(const double* __restrict__ D, 
     }
     *neg += c;
     return s;
+}
+
+static __device__ __noinline__ double dstqds_guarded(const double* parent, int n, double tau, double pivmin, double* out,
+                                             float* out_lo) {
+    double g = dstqds<double>(parent, n, tau, pivmin, out);
+    if (out && g < INFINITY) {
+        for (int i = 0; i < n; ++i) {
+            out_lo[i] = (float)out[i];
+            out_lo[n + i] = (float)out[3 * n + i];
+        }
+    }
+    return g;
+}
+
+// Child representation parent - tau I (stationary transform, as dstqds) with
+// the element growth max |d+_i| tracked on the bit patterns; if out != null
+// the child rep is written there and its rounded copy [D | LLD] to out_lo,
+// in the same pass.  Unguarded; a vanished pivot makes the result
+// non-finite and the guarded generic transform is used instead.
+__device__ __forceinline__ double dstqds_fast(const double* __restrict__ parent, int n, double tau, double pivmin,
+                                              double* __restrict__ out, float* __restrict__ out_lo) {
+    const double* __restrict__ D = parent;
+    const double* __restrict__ L = parent + n;
+    const double* __restrict__ LD = parent + 2 * n;
+    double s = -tau;
+    unsigned long long gmax = 0;
+    double dn = __ldg(D), ldn = __ldg(LD), lnx = __ldg(L);
+    for (int i = 0; i < n - 1; ++i) {
+        double di = dn, ldi = ldn, li = lnx;
+        dn = __ldg(D + i + 1);
+        ldn = __ldg(LD + i + 1);
+        lnx = __ldg(L + i + 1);
+        double dp = di + s;
+        unsigned long long a = dabsbits(dp);
+        gmax = a > gmax ? a : gmax;
+        double lp = ldi * drcp<2>(dp);
+        s = fma(lp * li, s, -tau);
+        if (out) {
+            double ldp = dp * lp;
+            double lldp = ldp * lp;
+            out[i] = dp;
+            out[n + i] = lp;
+            out[2 * n + i] = ldp;
+            out[3 * n + i] = lldp;
+            out_lo[i] = (float)dp;
+            out_lo[n + i] = (float)lldp;
+        }
+    }
+    double dp = dn + s;
+    unsigned long long a = dabsbits(dp);
+    gmax = a > gmax ? a : gmax;
+    if (!dfinite(s) || !dfinite(dp) || gmax >= 0x7ff0000000000000ULL)
+        return dstqds_guarded(parent, n, tau, pivmin, out, out_lo);
+    if (out) {
+        out[n - 1] = dp;
+        out[2 * n - 1] = 0.0;
+        out[3 * n - 1] = 0.0;
+        out[4 * n - 1] = 0.0;
+        out_lo[n - 1] = (float)dp;
+        out_lo[2 * n - 1] = 0.0f;
+    }
+    return __longlong_as_double((long long)gmax);
 }
 
 // N_r^T z = e_r from l+ (A, rows < r) and u (B, rows >= r); z overwrites A.
@@ -162,6 +244,27 @@ __device__ __forceinline__ double solve_twisted_fast(const double* __restrict__ 
     }
     *imax = im;
     return nrm2;
+}
+
+// Guarded generic twisted solve (out of line), with the arg-max of |z|.
+static __device__ __noinline__ TwistResult<double> twisted_guarded(const double* rep, int n, double lam, double pivmin,
+                                                            double* A, double* B, double* gamma, int* imax) {
+    Scratch<double> W;
+    W.a = A;
+    W.b = B;
+    W.stride = 1;
+    TwistResult<double> res = twisted_solve<double>(rep, n, lam, pivmin, W, gamma);
+    unsigned long long zb = 0;
+    int im = 0;
+    for (int i = 0; i < n; ++i) {
+        unsigned long long a = dabsbits(A[i]);
+        if (a > zb) {
+            zb = a;
+            im = i;
+        }
+    }
+    *imax = im;
+    return res;
 }
 
 // One twisted-factorization solve at lam for an eigenpair whose scratch
@@ -263,25 +366,7 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
         neg += dsign(gbest);
         bad = !dfinite(s) || !dfinite(p) || !dfinite(gbest);
     }
-    if (bad) {
-        // a pivot vanished: redo with the guarded generic transform
-        Scratch<double> W;
-        W.a = A;
-        W.b = B;
-        W.stride = 1;
-        res = twisted_solve<double>(rep, n, lam, pivmin, W, gamma);
-        unsigned long long zb = 0;
-        int im = 0;
-        for (int i = 0; i < n; ++i) {
-            unsigned long long a = dabsbits(A[i]);
-            if (a > zb) {
-                zb = a;
-                im = i;
-            }
-        }
-        *imax = im;
-        return res;
-    }
+    if (bad) return twisted_guarded(rep, n, lam, pivmin, A, B, gamma, imax);
     res.nrm2 = solve_twisted_fast(LD, n, r, A, B, imax);
     res.r = r;
     res.neg = neg;

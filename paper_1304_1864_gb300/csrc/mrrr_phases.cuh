@@ -580,6 +580,24 @@ MRRR_HD double weighted_growth(const Y* parent, int n, Y tau, Y pm, Y* work) {
     return isfinite(r) ? r : INFINITY;
 }
 
+// Child rep parent - tau I and its rounded low-precision copy; returns the
+// element growth.  The device binary64 path builds both in one pass.
+template <class Y, class Lo>
+MRRR_HD double child_transform(const Y* parent, int n, Y tau, Y pm, Y* out, Lo* out_lo) {
+#if defined(__CUDA_ARCH__)
+    if constexpr (std::is_same<Y, double>::value && std::is_same<Lo, float>::value)
+        return dstqds_fast(parent, n, tau, to_d(pm), out, out_lo);
+#endif
+    double g = dstqds<Y>(parent, n, tau, pm, out);
+    if (out) {
+        for (int i = 0; i < n; ++i) {
+            out_lo[i] = (Lo)to_d(out[i]);
+            out_lo[n + i] = (Lo)to_d(out[3 * n + i]);
+        }
+    }
+    return g;
+}
+
 // New RRR for a cluster (Algorithm 1, lines 15-17): a shift tau just outside
 // the left or right end of the cluster, child = parent - tau I by the
 // stationary transform in working precision.  Candidates back off from the
@@ -621,7 +639,7 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
             double tau = side == 0 ? lo - delta : hi + delta;
             // the first candidate is usually accepted: build it in place
             bool store = (k == 0 && side == 0);
-            double g = dstqds<Y>(parent, n, from_d<Y>(tau), pm, store ? child : (Y*)nullptr);
+            double g = child_transform<Y, Lo>(parent, n, from_d<Y>(tau), pm, store ? child : (Y*)nullptr, child_lo);
             if (store) stored_tau = tau;
             steps += n;
             if (g <= bound) {
@@ -646,12 +664,8 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     }
     if (!accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
     if (!(stored_tau == best_tau)) {
-        dstqds<Y>(parent, n, from_d<Y>(best_tau), pm, child);
+        child_transform<Y, Lo>(parent, n, from_d<Y>(best_tau), pm, child, child_lo);
         steps += n;
-    }
-    for (int i = 0; i < n; ++i) {
-        child_lo[i] = (Lo)to_d(child[i]);
-        child_lo[n + i] = (Lo)to_d(child[3 * n + i]);
     }
     MRRR_ATOMIC_ADD(&C->qd_shift, steps);
     // sigma_child = sigma_parent + tau, kept as an unevaluated double pair
@@ -748,13 +762,23 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
                 break;
             }
             Y nl = lam + corr;
-            if (!(lo < nl && nl < hi)) break;  // left the bracket: fall back to bisection
-            lam = nl;
+            if (lo < nl && nl < hi) {
+                lam = nl;
+            } else {
+                // the correction left the bracket (it points at another
+                // eigenvalue): take a bisection step instead, with the bracket
+                // just narrowed by the inertia at lam, and refactor fully
+                lam = (lo + hi) * from_d<Y>(0.5);
+                r_hint = -1;
+            }
         }
         if (!conv) {
             MRRR_ATOMIC_ADD(&C->fallbacks, 1);
             double rt = cfg.mixed ? cfg.eps_x * sq * cfg.gaptol : n * cfg.eps_y;
             rt = fmax(rt, 4.0 * cfg.eps_y);
+            // bisection: first with the fast count, then the last bits with the
+            // fully accurate one
+            steps += bisect_bracket<Y, Y, true>(rep, n, I.j, lo, hi, B.pivmin, fmax(rt, 1e-12), 1, 600);
             steps += bisect_bracket<Y, Y>(rep, n, I.j, lo, hi, B.pivmin, rt, 1, 600);
             lam = (lo + hi) * from_d<Y>(0.5);
             tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t, -1);

@@ -209,3 +209,24 @@ def test_batch_equals_individual(prec):
     for (dd, ee), (Wb, Zb) in zip(mats, out):
         W1, Z1, _ = m.solve(dd, ee, mode="mixed")
         assert torch.equal(W1, Wb) and torch.equal(Z1, Zb)
+
+
+def test_batched_workload_subsample():
+    # independent tridiagonals of uneven size and type in one batched call:
+    # n log-uniform in [32, 2048], types {U(-1,1), 1-2-1, Wilkinson, glued W_21}
+    import paper_1304_1864_gb300 as m
+    batch = inputs.workload_c4(count=48, seed=4)
+    mats = [(torch.tensor(d, dtype=torch.float32, device="cuda"), torch.tensor(e, dtype=torch.float32, device="cuda"))
+            for _, d, e in batch]
+    out, st, status = m.solve_batch(mats, mode="mixed")
+    assert all(s == 0 for s in status), status
+    rng = np.random.default_rng(7)
+    for (kind, d, e), (W, Z) in zip(batch, out):
+        d64, e64 = _acc.exact_input(d, e, "s")
+        W = _acc.as_np(W)
+        Z = _acc.as_np(Z)
+        n = d64.size
+        assert W.size == n and np.all(np.diff(W) >= 0)
+        idx = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 6)]))
+        _acc.check_eigvals(d64, e64, W, "s", "mixed", idx=idx)
+        _acc.check_res_orth(d64, e64, W, Z, "s", "mixed")
