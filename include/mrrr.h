@@ -89,6 +89,7 @@ typedef struct {
     long long qd_shift;   /* qd steps in building child representations */
     long long qd_low;     /* qd steps of the pre-bisection in a precision below the working one */
     int verify_fail;      /* pre-bisection brackets widened by the working-precision check */
+    int reps_relaxed;     /* child reps accepted only under the relaxed growth bound of Eq. (3.6) */
     int timed;            /* 1 if phase_ms / phase_launches were measured (MRRR_FLAG_TIMING) */
     int phase_launches[MRRR_NPHASES]; /* kernel launches per phase */
     double phase_ms[MRRR_NPHASES];    /* device time per phase (CUDA events on the solve's stream) */
@@ -110,8 +111,9 @@ typedef struct {
 
 /* Variant bits for mrrr_params.flags. */
 #define MRRR_FLAG_NO_LOWPREC_BISECT 1 /* never pre-bracket eigenvalues in a lower precision */
-#define MRRR_FLAG_IEEE_DIV 2          /* use correctly rounded division in the qd recurrences */
 #define MRRR_FLAG_TIMING 4            /* time every phase with CUDA events (fills stats->phase_ms) */
+#define MRRR_FLAG_STRICT_GROWTH 8     /* MIXED: accept child reps only under the y = x growth bound,
+                                         not the relaxed bound of Sec. 3.2, Eq. (3.6) */
 
 /*
  * Single-precision input/output (x = binary32).  MRRR_MIXED computes in

@@ -607,7 +607,8 @@ MRRR_HD double child_transform(const Y* parent, int n, Y tau, Y pm, Y* out, Lo* 
 // growth weighted by an approximate cluster vector, is at most
 // growth_k * spdiam(root).  If no candidate passes, the one with the
 // smallest weighted growth is taken (Sec. 2, "Requirements on the
-// representations"; Sec. 4.1) and counted in reps_failed.  Members move to
+// representations"; Sec. 4.1) and counted in reps_failed.  In mixed precision
+// the plain growth test uses the relaxed bound of Eq. (3.6).  Members move to
 // the child: rep (and its low-precision copy), sigma += tau, brackets
 // shifted by -tau (re-verified by the refinement that follows).
 template <class Y, class Lo>
@@ -627,6 +628,11 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     double base = fmax(fmax(0.25 * span, 2.0 * bw), 4.0 * cfg.eps_y * fmax(fabs(lo), fabs(hi)));
     base = fmax(base, 4.0 * B.pivmin);
     const double bound = cfg.growth_k * B.spdiam;
+    // Sec. 3.2, Eq. (3.6): with y > x the element growth may reach
+    // max{10, eps_x / (eps_y sqrt(n))} spdiam without loss of accuracy
+    const double relaxed = (cfg.mixed && !(cfg.flags & 8 /* MRRR_FLAG_STRICT_GROWTH */))
+                               ? fmax(cfg.growth_k, cfg.eps_x / (cfg.eps_y * sqrt((double)n))) * B.spdiam
+                               : bound;
     double best_w = INFINITY, best_tau = lo - base;
     double stored_tau = NAN;  // the candidate whose child rep is in `child`
     bool accepted = false;
@@ -642,9 +648,10 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
             double g = child_transform<Y, Lo>(parent, n, from_d<Y>(tau), pm, store ? child : (Y*)nullptr, child_lo);
             if (store) stored_tau = tau;
             steps += n;
-            if (g <= bound) {
+            if (g <= relaxed) {
                 best_tau = tau;
                 accepted = true;
+                if (g > bound) MRRR_ATOMIC_ADD(&C->reps_relaxed, 1);
                 break;
             }
             // child storage doubles as work space for the weighted test

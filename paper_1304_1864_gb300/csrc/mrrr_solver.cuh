@@ -242,6 +242,67 @@ __global__ void k_bisect_lo(Item* items, const int* list, int count, const Block
     if (s) atomicAdd(&C->qd_steps_low, s);
 }
 
+// Multisection variant of the low-precision pre-bisection: kMS lanes per
+// item evaluate the count at kMS interior points of the same bracket in one
+// sweep, so each sweep gains log2(kMS + 1) bits instead of one.  The sweeps
+// are sequential in the row index, so this trades spare low-precision
+// throughput for latency.  Lanes of one item are adjacent in a warp and share
+// their counts by shuffles; every lane of the group keeps the same bracket.
+constexpr int kMS = 4;
+template <class Lo>
+__global__ void k_bisect_lo_ms(Item* items, const int* list, int count, const BlockDesc* blocks, double wrel,
+                               DevCounters* C) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int g = t / kMS, q = t % kMS;
+    if (g >= count) return;  // whole groups leave together (kMS divides 32)
+    unsigned mask = ((1u << kMS) - 1u) << ((threadIdx.x & 31) & ~(kMS - 1));
+    Item& I = items[list ? list[g] : g];
+    const int n = I.n;
+    if (n == 1) return;
+    const Lo* D = (const Lo*)I.rep_lo;
+    const Lo* LLD = D + n;
+    Lo pm = (Lo)fmax(blocks[I.block].pivmin, (double)Prec<Lo>::tiny * 4.0);
+    double lo = I.lo, hi = I.hi;
+    unsigned long long steps = 0;
+    for (int it = 0; it < 64; ++it) {
+        if (!(hi - lo > wrel * fmax(fabs(lo), fabs(hi)))) break;
+        double w = (hi - lo) / (kMS + 1);
+        Lo x = (Lo)(lo + w * (q + 1));
+        bool inside = (double)x > lo && (double)x < hi;
+        int c = inside ? negcount_lo<Lo>(D, LLD, n, x, pm) : (q < kMS / 2 ? -1 : n + 1);
+        if (inside) steps += (unsigned long long)n;
+        // the first point (left to right) whose count reaches j is the new
+        // upper end and the point before it the new lower end -- well defined
+        // even where rounding makes the low-precision count non-monotone
+        double nlo = lo, nhi = hi;
+        bool any_inside = false, found = false;
+#pragma unroll
+        for (int k = 0; k < kMS; ++k) {
+            int ck = __shfl_sync(mask, c, k, kMS);
+            double xk = __shfl_sync(mask, (double)x, k, kMS);
+            bool ik = __shfl_sync(mask, (int)inside, k, kMS) != 0;
+            any_inside |= ik;
+            if (!ik || found) continue;
+            if (ck >= I.j) {
+                nhi = xk;
+                found = true;
+            } else {
+                nlo = xk;
+            }
+        }
+        if (!any_inside) break;  // no representable interior point left
+        lo = nlo;
+        hi = nhi;
+    }
+    if (q == 0) {
+        I.lo = lo;
+        I.hi = hi;
+        if (steps) atomicAdd(&C->qd_steps_low, steps);
+    } else if (steps) {
+        atomicAdd(&C->qd_steps_low, steps);
+    }
+}
+
 // Two threads per item: one per end of the bracket.
 template <class Y>
 __global__ void k_verify(Item* items, const int* list, int count, const BlockDesc* blocks, DevCounters* C,
@@ -428,7 +489,7 @@ template <class X, class Y>
 int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
                 mrrr_stats* stats) {
     typedef typename LowOf<Y>::T Lo;
-    const bool use_low = LowOf<Y>::use;
+    const bool use_low = LowOf<Y>::use && !(cfg.flags & MRRR_FLAG_NO_LOWPREC_BISECT);
     // relative width of the low-precision pre-bisection
     const double wrel_lo = std::is_same<Lo, float>::value ? 0x1p-19 : cfg.rtol_class;
     long long N = 0;
@@ -511,7 +572,8 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 tl.begin(phase);
                 int launches = 0;
                 if (use_low) {
-                    k_bisect_lo<Lo><<<grid_for(count), kThreads, 0, st>>>(items, list, count, d_blocks, wrel_lo, d_C);
+                    k_bisect_lo_ms<Lo><<<grid_for((long long)count * kMS), kThreads, 0, st>>>(items, list, count,
+                                                                                          d_blocks, wrel_lo, d_C);
                     k_verify<Y><<<grid_for(2LL * count), kThreads, 0, st>>>(items, list, count, d_blocks, d_C, ctr);
                     MRRR_CK(cudaMemsetAsync(&d_C->nrefine, 0, sizeof(int), st));
                     k_certify<<<grid_for(count), kThreads, 0, st>>>(items, K, list, count, cfg.gaptol, refine_list,
@@ -627,6 +689,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         stats->qd_shift = (long long)C.qd_shift;
         stats->qd_low = (long long)C.qd_steps_low;
         stats->verify_fail = C.verify_fail;
+        stats->reps_relaxed = C.reps_relaxed;
         tl.collect(stats);
     }
     if (arena.failed) return MRRR_ERR_NOMEM;

@@ -114,6 +114,7 @@ struct DevCounters {
     int d_max;
     int forced;
     int verify_fail;    // low-precision brackets that failed verification and were widened
+    int reps_relaxed;   // child reps accepted only under the relaxed growth bound of Eq. (3.6)
     int nrefine;        // items needing working-precision refinement at the current step
 };
 
