@@ -39,6 +39,7 @@ using std::fmin;
 using std::frexp;
 using std::isfinite;
 using std::ldexp;
+using std::nextafter;
 using std::sqrt;
 #endif
 

@@ -277,6 +277,10 @@ MRRR_HD void init_item(const BlockDesc& B, int bidx, Item& I, int t, const Y* re
     I.depth = 0;
     I.kind = KIND_OPEN;
     I.wanted = (I.j >= B.w_lo && I.j <= B.w_hi) ? 1 : 0;  // refined by assign_col
+    I.lam_hi = 0.0;
+    I.lam_lo = 0.0;
+    I.rqi_done = 0;
+    I.rhint = -1;
 }
 
 // --------------------------------------------------------------- a3: bisection
@@ -721,9 +725,15 @@ MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratc
 // gives the vector (Sec. 3.2, "Rayleigh quotient iteration").  The vector is
 // normalised, signed (largest entry positive), rounded to x and stored with
 // lambda + sigma (Algorithm 1, line 11; Sec. 3.3).
+//
+// The iteration runs in passes of at most pass_iters steps: an eigenpair not
+// converged at the end of a pass (and not in the final pass) saves its shift,
+// bracket and twist index in I and returns false ("parked"), so that the few
+// slow eigenpairs continue in a later, densely packed launch instead of
+// holding a whole warp.  Returns true when the eigenpair was stored.
 template <class X, class Y>
-MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const SolveCfg& cfg,
-                      const Scratch<Y>& Wk, DevCounters* C) {
+MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const SolveCfg& cfg,
+                      const Scratch<Y>& Wk, DevCounters* C, int pass_iters, bool final_pass) {
     typedef typename Acc<Y>::T A_t;
     MatrixDesc& M = mats[I.matrix];
     const BlockDesc& B = blocks[I.block];
@@ -736,6 +746,10 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     const double tol = cfg.mixed ? cfg.krs * gap * cfg.eps_x * sq : cfg.krs * gap * n * cfg.eps_y / cfg.gaptol;
     Y lo = from_d<Y>(I.lo), hi = from_d<Y>(I.hi);
     Y lam = (lo + hi) * from_d<Y>(0.5);
+    if (I.rqi_done > 0) {  // continue from the saved shift
+        if constexpr (std::is_same<Y, dd>::value) lam = dd(I.lam_hi, I.lam_lo);
+        else lam = from_d<Y>(I.lam_hi);
+    }
     Y gamma = from_d<Y>(0.0);
     TwistResult<Y> tr;
     Y lam_out = lam;
@@ -752,8 +766,9 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     } else {
         // after the first step the twist index is the largest entry of the
         // previous iterate (one pass of the transforms instead of two)
-        int r_hint = -1;
-        for (int it = 0; it < cfg.max_rqi; ++it) {
+        int r_hint = I.rhint;
+        const int done0 = I.rqi_done;
+        for (int it = 0; it < pass_iters && done0 + it < cfg.max_rqi; ++it) {
             tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t, r_hint);
             steps += (r_hint < 0 ? 2ULL : 1ULL) * n;
             r_hint = imax_t;
@@ -778,6 +793,24 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
                 lam = (lo + hi) * from_d<Y>(0.5);
                 r_hint = -1;
             }
+        }
+        if (!conv && !final_pass && done0 + iters < cfg.max_rqi) {
+            // park: save the state, rounding the bracket outward to binary64
+            double lod = to_d(lo), hid = to_d(hi);
+            I.lo = nextafter(lod, -INFINITY);
+            I.hi = nextafter(hid, INFINITY);
+            if constexpr (std::is_same<Y, dd>::value) {
+                I.lam_hi = lam.hi;
+                I.lam_lo = lam.lo;
+            } else {
+                I.lam_hi = to_d(lam);
+                I.lam_lo = 0.0;
+            }
+            I.rqi_done = done0 + iters;
+            I.rhint = r_hint;
+            MRRR_ATOMIC_ADD(&C->rqi_iters, iters);
+            MRRR_ATOMIC_ADD(&C->qd_rqi, steps);
+            return false;
         }
         if (!conv) {
             MRRR_ATOMIC_ADD(&C->fallbacks, 1);
@@ -834,6 +867,7 @@ MRRR_HD void rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         for (int i = 0; i < n; ++i) Z[i] = (X)(to_d(Wk.A(i)) * inv);
     }
     ((X*)M.W)[I.outcol] = (X)lam_T;
+    return true;
 }
 
 // --------------------------------------------------------------- ordering of W

@@ -350,19 +350,27 @@ __global__ void k_shift(const Cluster* clusters, int nc, Item* items, const Bloc
     shift_cluster<Y, Lo>(clusters[t], items, blocks, pool, pool_lo, cfg, C);
 }
 
+// One thread per eigenpair of the list (or of *count_dev entries of it):
+// at most pass_iters RQI steps; unfinished eigenpairs go to park_list.
 template <class X, class Y>
-__global__ void k_rqi(Item* items, const int* list, int count, MatrixDesc* mats, const BlockDesc* blocks,
-                      SolveCfg cfg, Y* scratch, int nmax, DevCounters* C) {
+__global__ void k_rqi(Item* items, const int* list, int count, const int* count_dev, MatrixDesc* mats,
+                      const BlockDesc* blocks, SolveCfg cfg, Y* scratch, int nmax, DevCounters* C, int pass_iters,
+                      int final_pass, int* park_list, int* park_count) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (count_dev) count = min(count, *count_dev);
     if (t >= count) return;
-    Item& I = items[list[t]];
+    const int it = list[t];
+    Item& I = items[it];
     // each eigenpair owns two contiguous arrays of nmax words
     Scratch<Y> Wk;
     Y* base = scratch + (size_t)t * (size_t)(2 * nmax);
     Wk.a = base;
     Wk.b = base + nmax;
     Wk.stride = 1;
-    rqi_item<X, Y>(I, mats, blocks, cfg, Wk, C);
+    if (!rqi_item<X, Y>(I, mats, blocks, cfg, Wk, C, pass_iters, final_pass != 0)) {
+        int slot = atomicAdd(park_count, 1);
+        park_list[slot] = it;
+    }
 }
 
 template <class X>
@@ -595,20 +603,44 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             tl.end();
             MRRR_CK(cudaGetLastError());
             size_t per = 2 * (size_t)nmax * sizeof(Y);
+            // RQI in passes: two steps per eigenpair in the first pass (most
+            // converge), then the parked ones, densely packed, in further passes
             auto run_rqi = [&](int s0, int s1, cudaStream_t rs) -> int {
                 if (s1 <= s0) return 0;
+                const int S = s1 - s0;
                 long long wave = (long long)(ScratchBudget<Y>::bytes() / 2 / per);
                 wave = std::max<long long>(32, wave / 32 * 32);
-                wave = std::min<long long>(wave, ((long long)(s1 - s0) + 31) / 32 * 32);
+                wave = std::min<long long>(wave, ((long long)S + 31) / 32 * 32);
                 Y* scratch = arena.alloc<Y>((size_t)wave * 2 * nmax);
-                if (!scratch) return MRRR_ERR_NOMEM;
-                for (long long w0 = s0; w0 < s1; w0 += wave) {
-                    int cnt = (int)std::min<long long>(wave, s1 - w0);
-                    tl.begin(MRRR_PHASE_RQI, rs);
-                    k_rqi<X, Y><<<grid_for(cnt), kThreads, 0, rs>>>(items, single_list + w0, cnt, d_mats, d_blocks,
-                                                                    cfg, scratch, nmax, d_C);
-                    tl.end(1, rs);
-                    if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
+                int* park = arena.alloc<int>(2 * (size_t)S + 2);
+                if (!scratch || !park) return MRRR_ERR_NOMEM;
+                int* park_a = park;
+                int* park_b = park + S;
+                int* counts = park + 2 * (size_t)S;  // two device counters
+                const int kPasses = 3;
+                const int* list = single_list + s0;
+                int count = S;
+                for (int pass = 0; pass < kPasses && count > 0; ++pass) {
+                    bool final_pass = pass == kPasses - 1;
+                    int* out = (pass % 2 == 0) ? park_a : park_b;
+                    int* cnt = counts + (pass % 2);
+                    if (cudaMemsetAsync(cnt, 0, sizeof(int), rs) != cudaSuccess) return MRRR_ERR_CUDA;
+                    for (long long w0 = 0; w0 < count; w0 += wave) {
+                        int c = (int)std::min<long long>(wave, count - w0);
+                        tl.begin(MRRR_PHASE_RQI, rs);
+                        k_rqi<X, Y><<<grid_for(c), kThreads, 0, rs>>>(items, list + w0, c, nullptr, d_mats, d_blocks, cfg,
+                                                                      scratch, nmax, d_C, pass == 0 ? 2 : 3,
+                                                                      final_pass ? 1 : 0, out, cnt);
+                        tl.end(1, rs);
+                        if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
+                    }
+                    if (final_pass) break;
+                    int h = 0;
+                    if (cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, rs) != cudaSuccess ||
+                        cudaStreamSynchronize(rs) != cudaSuccess)
+                        return MRRR_ERR_CUDA;
+                    list = out;
+                    count = h;
                 }
                 return 0;
             };

@@ -81,6 +81,10 @@ struct Item {
     int depth;          // depth of the current rep in the representation tree
     int kind;           // KIND_*
     int wanted;         // 1 if the eigenpair is returned, 0 if only a neighbour
+    // Rayleigh quotient iteration state carried between passes
+    double lam_hi, lam_lo;  // current shift (hi + lo)
+    int rqi_done;       // iterations done so far
+    int rhint;          // twist index for the next iteration (-1: full factorization)
 };
 
 enum : int { KIND_OPEN = 0, KIND_SINGLETON = 1, KIND_CLUSTER = 2, KIND_DROPPED = 3 };
@@ -116,6 +120,7 @@ struct DevCounters {
     int verify_fail;    // low-precision brackets that failed verification and were widened
     int reps_relaxed;   // child reps accepted only under the relaxed growth bound of Eq. (3.6)
     int nrefine;        // items needing working-precision refinement at the current step
+    int npark;          // eigenpairs parked for the next RQI pass
 };
 
 }  // namespace mrrr

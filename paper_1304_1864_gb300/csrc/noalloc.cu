@@ -136,6 +136,7 @@ __global__ void k_noalloc_rqi(unsigned char* base, const float* W, int il, int k
     I.outcol = t;
     I.sig_hi = B.mu;
     I.wanted = 1;
+    I.rhint = -1;
     int fails = 0;
     verify_endpoint<double>(I, B, 0, &fails);
     verify_endpoint<double>(I, B, 1, &fails);
@@ -146,7 +147,7 @@ __global__ void k_noalloc_rqi(unsigned char* base, const float* W, int il, int k
     Wk.a = (double*)(base + kOffWork) + (size_t)t * 2 * kMaxN;
     Wk.b = Wk.a + kMaxN;
     Wk.stride = 1;
-    rqi_item<float, double>(I, &M, blocks, cfg, Wk, C);
+    rqi_item<float, double>(I, &M, blocks, cfg, Wk, C, cfg.max_rqi, true);
 }
 
 // Device address of the scratch array, looked up once per device with that
