@@ -730,10 +730,14 @@ MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratc
 // converged at the end of a pass (and not in the final pass) saves its shift,
 // bracket and twist index in I and returns false ("parked"), so that the few
 // slow eigenpairs continue in a later, densely packed launch instead of
-// holding a whole warp.  Returns true when the eigenpair was stored.
+// holding a whole warp.  Returns true when the eigenpair was stored.  With
+// store_scale != null (binary64 and binary32 working precision) the vector
+// is left unnormalised in the scratch and the factor 1/||z|| (with the sign)
+// is returned there for a warp-cooperative store.
 template <class X, class Y>
 MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const SolveCfg& cfg,
-                      const Scratch<Y>& Wk, DevCounters* C, int pass_iters, bool final_pass) {
+                      const Scratch<Y>& Wk, DevCounters* C, int pass_iters, bool final_pass,
+                      double* store_scale = nullptr) {
     typedef typename Acc<Y>::T A_t;
     MatrixDesc& M = mats[I.matrix];
     const BlockDesc& B = blocks[I.block];
@@ -797,8 +801,8 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         if (!conv && !final_pass && done0 + iters < cfg.max_rqi) {
             // park: save the state, rounding the bracket outward to binary64
             double lod = to_d(lo), hid = to_d(hi);
-            I.lo = nextafter(lod, -INFINITY);
-            I.hi = nextafter(hid, INFINITY);
+            I.lo = nextafter(lod, -HUGE_VAL);
+            I.hi = nextafter(hid, HUGE_VAL);
             if constexpr (std::is_same<Y, dd>::value) {
                 I.lam_hi = lam.hi;
                 I.lam_lo = lam.lo;
@@ -820,14 +824,32 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
             // fully accurate one
             steps += bisect_bracket<Y, Y, true>(rep, n, I.j, lo, hi, B.pivmin, fmax(rt, 1e-12), 1, 600);
             steps += bisect_bracket<Y, Y>(rep, n, I.j, lo, hi, B.pivmin, rt, 1, 600);
+            // then a few safeguarded RQI steps from the midpoint, which now
+            // lies close enough for the iteration to settle
             lam = (lo + hi) * from_d<Y>(0.5);
-            tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t, -1);
-            steps += 2ULL * n;
-            ++iters;
-            double nrm2 = to_d(tr.nrm2);
-            double resid = fabs(to_d(gamma)) / sqrt(nrm2);
-            lam_out = lam + gamma / Y(tr.nrm2);
-            conv = resid <= fmax(tol, 8.0 * cfg.eps_y * n * fabs(to_d(lam)));
+            int rh = -1;
+            for (int k = 0; k < 4; ++k) {
+                tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t, rh);
+                steps += (rh < 0 ? 2ULL : 1ULL) * n;
+                rh = imax_t;
+                ++iters;
+                if (tr.neg >= I.j) hi = bmin(hi, lam);
+                else lo = bmax(lo, lam);
+                double nrm2 = to_d(tr.nrm2);
+                double resid = fabs(to_d(gamma)) / sqrt(nrm2);
+                Y corr = gamma / Y(tr.nrm2);
+                lam_out = lam + corr;
+                conv = resid <= fmax(tol, 8.0 * cfg.eps_y * n * fabs(to_d(lam))) ||
+                       fabs(to_d(corr)) <= 4.0 * cfg.eps_y * fabs(to_d(lam));
+                if (conv) break;
+                Y nl = lam + corr;
+                if (lo < nl && nl < hi) {
+                    lam = nl;
+                } else {
+                    lam = (lo + hi) * from_d<Y>(0.5);
+                    rh = -1;
+                }
+            }
             if (!conv) {
                 MRRR_ATOMIC_ADD(&C->noconv, 1);
                 M.status = ST_ERR_NOCONV;  // every writer stores the same value
@@ -864,7 +886,11 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         }
     } else {
         double inv = sgn / to_d(nrm);
-        for (int i = 0; i < n; ++i) Z[i] = (X)(to_d(Wk.A(i)) * inv);
+        if (store_scale) {
+            *store_scale = inv;  // the caller stores z * inv (coalesced across a warp)
+        } else {
+            for (int i = 0; i < n; ++i) Z[i] = (X)(to_d(Wk.A(i)) * inv);
+        }
     }
     ((X*)M.W)[I.outcol] = (X)lam_T;
     return true;

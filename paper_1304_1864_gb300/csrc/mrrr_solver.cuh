@@ -350,26 +350,71 @@ __global__ void k_shift(const Cluster* clusters, int nc, Item* items, const Bloc
     shift_cluster<Y, Lo>(clusters[t], items, blocks, pool, pool_lo, cfg, C);
 }
 
-// One thread per eigenpair of the list (or of *count_dev entries of it):
-// at most pass_iters RQI steps; unfinished eigenpairs go to park_list.
+// One thread per eigenpair of the list: at most pass_iters RQI steps;
+// unfinished eigenpairs go to park_list.  Finished vectors are written by
+// the whole warp: a 32 x 32 tile (32 rows of the 32 lanes' vectors) goes
+// through shared memory so that each column segment is one contiguous
+// 128-byte (binary32) / 256-byte (binary64) store, instead of 32 scattered
+// words per instruction.
 template <class X, class Y>
-__global__ void k_rqi(Item* items, const int* list, int count, const int* count_dev, MatrixDesc* mats,
+__global__ void k_rqi(Item* items, const int* list, int w0, int count, const int* dev_total, MatrixDesc* mats,
                       const BlockDesc* blocks, SolveCfg cfg, Y* scratch, int nmax, DevCounters* C, int pass_iters,
                       int final_pass, int* park_list, int* park_count) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (count_dev) count = min(count, *count_dev);
-    if (t >= count) return;
-    const int it = list[t];
-    Item& I = items[it];
-    // each eigenpair owns two contiguous arrays of nmax words
+    constexpr bool kCoop = !std::is_same<Y, dd>::value;
+    __shared__ X tile[kThreads / 32][32][33];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    // list[w0 .. w0+count) is this launch's share; a later pass is launched
+    // for an upper bound and reads the true length of its list on the device
+    const bool active = t < count && (dev_total == nullptr || w0 + t < *dev_total);
+    if (!kCoop && !active) return;
+    int it = active ? list[w0 + t] : 0;
     Scratch<Y> Wk;
-    Y* base = scratch + (size_t)t * (size_t)(2 * nmax);
+    Y* base = scratch + (size_t)(active ? t : 0) * (size_t)(2 * nmax);
     Wk.a = base;
     Wk.b = base + nmax;
     Wk.stride = 1;
-    if (!rqi_item<X, Y>(I, mats, blocks, cfg, Wk, C, pass_iters, final_pass != 0)) {
-        int slot = atomicAdd(park_count, 1);
-        park_list[slot] = it;
+    double scale = 0.0;
+    bool stored = false;
+    if (active) {
+        Item& I = items[it];
+        stored = rqi_item<X, Y>(I, mats, blocks, cfg, Wk, C, pass_iters, final_pass != 0, kCoop ? &scale : nullptr);
+        if (!stored) {
+            int slot = atomicAdd(park_count, 1);
+            park_list[slot] = it;
+        }
+    }
+    if constexpr (kCoop) {
+        // warp-cooperative store of the finished vectors
+        int nrow = 0, ldz = 0;
+        X* col = nullptr;
+        if (stored) {
+            const Item& I = items[it];
+            const MatrixDesc& M = mats[I.matrix];
+            nrow = I.n;
+            ldz = M.ldz;
+            col = (X*)M.Z + (size_t)I.outcol * (size_t)ldz + blocks[I.block].mrow;
+        }
+        (void)ldz;
+        int nmaxw = nrow;
+        for (int o = 16; o > 0; o >>= 1) nmaxw = max(nmaxw, __shfl_xor_sync(0xffffffffu, nmaxw, o));
+        for (int r0 = 0; r0 < nmaxw; r0 += 32) {
+            // lane l: rows r0..r0+31 of its own vector into tile row l
+#pragma unroll 4
+            for (int q = 0; q < 32; ++q) {
+                int r = r0 + q;
+                tile[wib][lane][q] = (r < nrow) ? (X)(to_d(Wk.a[r]) * scale) : X(0);
+            }
+            __syncwarp();
+            // column c of the tile: lanes write 32 consecutive rows
+            for (int c = 0; c < 32; ++c) {
+                X* cc = (X*)__shfl_sync(0xffffffffu, (unsigned long long)col, c);
+                int nc = __shfl_sync(0xffffffffu, nrow, c);
+                int r = r0 + lane;
+                if (cc && r < nc) cc[r] = tile[wib][c][lane];
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -604,7 +649,8 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             MRRR_CK(cudaGetLastError());
             size_t per = 2 * (size_t)nmax * sizeof(Y);
             // RQI in passes: two steps per eigenpair in the first pass (most
-            // converge), then the parked ones, densely packed, in further passes
+            // converge), then the parked ones, densely packed, in further
+            // passes; the last pass has the rest of the max_rqi budget
             auto run_rqi = [&](int s0, int s1, cudaStream_t rs) -> int {
                 if (s1 <= s0) return 0;
                 const int S = s1 - s0;
@@ -619,28 +665,26 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 int* counts = park + 2 * (size_t)S;  // two device counters
                 const int kPasses = 3;
                 const int* list = single_list + s0;
-                int count = S;
-                for (int pass = 0; pass < kPasses && count > 0; ++pass) {
+                const int* total = nullptr;  // the first pass has all S items
+                // no host synchronisation between passes: the stream (possibly
+                // the side stream) keeps running while the host goes on
+                for (int pass = 0; pass < kPasses; ++pass) {
                     bool final_pass = pass == kPasses - 1;
                     int* out = (pass % 2 == 0) ? park_a : park_b;
                     int* cnt = counts + (pass % 2);
-                    if (cudaMemsetAsync(cnt, 0, sizeof(int), rs) != cudaSuccess) return MRRR_ERR_CUDA;
-                    for (long long w0 = 0; w0 < count; w0 += wave) {
-                        int c = (int)std::min<long long>(wave, count - w0);
+                    if (!final_pass && cudaMemsetAsync(cnt, 0, sizeof(int), rs) != cudaSuccess) return MRRR_ERR_CUDA;
+                    int iters = pass == 0 ? 2 : (final_pass ? cfg.max_rqi : 3);
+                    for (long long w0 = 0; w0 < S; w0 += wave) {
+                        int c = (int)std::min<long long>(wave, S - w0);
                         tl.begin(MRRR_PHASE_RQI, rs);
-                        k_rqi<X, Y><<<grid_for(c), kThreads, 0, rs>>>(items, list + w0, c, nullptr, d_mats, d_blocks, cfg,
-                                                                      scratch, nmax, d_C, pass == 0 ? 2 : 3,
+                        k_rqi<X, Y><<<grid_for(c), kThreads, 0, rs>>>(items, list, (int)w0, c, total, d_mats, d_blocks,
+                                                                      cfg, scratch, nmax, d_C, iters,
                                                                       final_pass ? 1 : 0, out, cnt);
                         tl.end(1, rs);
                         if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
                     }
-                    if (final_pass) break;
-                    int h = 0;
-                    if (cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, rs) != cudaSuccess ||
-                        cudaStreamSynchronize(rs) != cudaSuccess)
-                        return MRRR_ERR_CUDA;
                     list = out;
-                    count = h;
+                    total = cnt;
                 }
                 return 0;
             };
