@@ -374,6 +374,41 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
     return res;
 }
 
+// L D L^T factorization of T - mu I for the root representation (as
+// ldl_factor): d_0 = a_0 - mu, l_i = b_i / d_i, d_{i+1} = (a_{i+1} - mu) -
+// l_i b_i.  The chain from d_i to d_{i+1} is the reciprocal (two Newton
+// steps) and one FMA with b_i^2 formed off the chain; the definiteness and
+// finiteness tests and max |d_i| run on the bit patterns.  Returns max |d_i|,
+// or +inf if a pivot has the wrong sign, vanished or overflowed.
+__device__ __forceinline__ double ldl_factor_fast(const double* __restrict__ a, const double* __restrict__ b, int n,
+                                                  double mu, int sgn, double* __restrict__ rep) {
+    double* D = rep;
+    double* L = rep + n;
+    const int want = sgn < 0 ? 1 : 0;  // sign bit every pivot must have
+    double d = a[0] - mu;
+    unsigned long long gmax = 0;
+    bool bad = false;
+    double an = n > 1 ? a[1] : 0.0, bn = b[0];
+    for (int i = 0; i < n - 1; ++i) {
+        double ai1 = an, bi = bn;
+        if (i + 2 < n) an = a[i + 2];
+        if (i + 1 < n - 1) bn = b[i + 1];
+        unsigned long long ab = dabsbits(d);
+        bad |= (dsign(d) != want) | (ab == 0ULL) | !dfinite(d);
+        gmax = ab > gmax ? ab : gmax;
+        D[i] = d;
+        double r = drcp<2>(d);
+        L[i] = bi * r;
+        d = fma(-(bi * bi), r, ai1 - mu);
+    }
+    unsigned long long ab = dabsbits(d);
+    bad |= (dsign(d) != want) | (ab == 0ULL) | !dfinite(d);
+    gmax = ab > gmax ? ab : gmax;
+    D[n - 1] = d;
+    L[n - 1] = 0.0;
+    return bad ? INFINITY : __longlong_as_double((long long)gmax);
+}
+
 #endif  // __CUDACC__
 
 }  // namespace mrrr

@@ -98,28 +98,41 @@ MRRR_HD void prep_matrix(MatrixDesc& M, BlockDesc* blocks, double* wd, double* w
 // CTA can run the two candidate factorizations on two warps and the
 // element-wise work on all its threads.
 
-// Step 1 (one thread): Gershgorin bounds, pivmin, spectral diameter.
-template <class Y>
-MRRR_HD void root_bounds(BlockDesc& B, const double* wd, const double* we, double* gl_out, double* gu_out) {
+// Step 1: Gershgorin bounds, pivmin, spectral diameter.  The bounds of the
+// rows i0, i0 + stride, ... of the block are folded
+// into *gl / *gu, and the largest e_i^2 into *emax2 (min and max are exact,
+// so any split over threads gives the serial result).
+MRRR_HD void root_bounds_part(const BlockDesc& B, const double* wd, const double* we, int i0, int stride, double* gl,
+                              double* gu, double* emax2) {
     const int n = B.n;
     const double* a = wd + B.row0;
     const double* b = we + B.row0;
-    double gl = 0.0, gu = 0.0, emax2 = 0.0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = i0; i < n; i += stride) {
         double r = 0.0;
         if (i > 0) r += fabs(b[i - 1]);
         if (i < n - 1) {
             r += fabs(b[i]);
-            emax2 = fmax(emax2, b[i] * b[i]);
+            *emax2 = fmax(*emax2, b[i] * b[i]);
         }
-        double lo = a[i] - r, hi = a[i] + r;
-        if (i == 0 || lo < gl) gl = lo;
-        if (i == 0 || hi > gu) gu = hi;
+        *gl = fmin(*gl, a[i] - r);
+        *gu = fmax(*gu, a[i] + r);
     }
+}
+
+template <class Y>
+MRRR_HD void root_bounds_finish(BlockDesc& B, double gl, double gu, double emax2) {
     // 4x the smallest normal of the working precision keeps every reciprocal
     // of a guarded pivot finite
     B.pivmin = 4.0 * Prec<Y>::tiny * fmax(1.0, emax2);
     B.spdiam = gu - gl;
+}
+
+// Step 1 on one thread.
+template <class Y>
+MRRR_HD void root_bounds(BlockDesc& B, const double* wd, const double* we, double* gl_out, double* gu_out) {
+    double gl = INFINITY, gu = -INFINITY, emax2 = 0.0;
+    root_bounds_part(B, wd, we, 0, 1, &gl, &gu, &emax2);
+    root_bounds_finish<Y>(B, gl, gu, emax2);
     *gl_out = gl;
     *gu_out = gu;
 }
@@ -136,7 +149,12 @@ MRRR_HD double root_candidate(const BlockDesc& B, const double* wd, const double
     double delta = 4.0 * n * 1.1102230246251565e-16 * bnd + 4.0 * B.pivmin;
     for (int attempt = 0; attempt < 40; ++attempt) {
         double mu = side ? gu + delta : gl - delta;
-        double g = ldl_factor<Y>(wd + B.row0, we + B.row0, n, mu, side ? -1 : +1, rep);
+        double g;
+#if defined(__CUDA_ARCH__)
+        if constexpr (std::is_same<Y, double>::value) g = ldl_factor_fast(wd + B.row0, we + B.row0, n, mu, side ? -1 : +1, rep);
+        else
+#endif
+            g = ldl_factor<Y>(wd + B.row0, we + B.row0, n, mu, side ? -1 : +1, rep);
         if (g < INFINITY) {
             *mu_out = mu;
             return g;

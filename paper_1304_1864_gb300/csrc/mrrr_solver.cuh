@@ -18,6 +18,14 @@ namespace mrrr {
 
 constexpr int kThreads = 128;
 
+// Kernels that run one long serial recurrence per thread (bisection, RQI,
+// child shifts) are bound by the latency of their FP64 chains and by the
+// FP64 issue rate of each SM sub-partition, not by memory.  They launch
+// one-warp CTAs so that even a few thousand items spread over all 152 SMs
+// instead of piling into a few large CTAs.
+constexpr int kLatThreads = 32;
+// threads of the one-CTA-per-block root kernel
+constexpr int kRootThreads = 256;
 inline int grid_for(long long n, int threads = kThreads) { return (int)((n + threads - 1) / threads); }
 
 // ------------------------------------------------------------------ kernels
@@ -128,12 +136,35 @@ __global__ void k_prep(MatrixDesc* mats, BlockDesc* blocks, double* wd, double* 
 template <class Y, class Lo>
 __global__ void k_root(const int* blist, BlockDesc* blocks, const MatrixDesc* mats, const double* wd,
                        const double* we, Y* reps, Lo* reps_lo, SolveCfg cfg) {
+    constexpr int T = kRootThreads;
     __shared__ double s_gl, s_gu, s_g[2], s_mu[2];
+    __shared__ double r_gl[T], r_gu[T], r_e2[T];
     BlockDesc& B = blocks[blist[blockIdx.x]];
     const MatrixDesc& M = mats[B.matrix];
     const int n = B.n;
-    if (threadIdx.x == 0) root_bounds<Y>(B, wd, we, &s_gl, &s_gu);
-    __syncthreads();
+    {
+        // Gershgorin bounds: strided partials, then a tree reduction
+        double gl = INFINITY, gu = -INFINITY, e2 = 0.0;
+        root_bounds_part(B, wd, we, threadIdx.x, T, &gl, &gu, &e2);
+        r_gl[threadIdx.x] = gl;
+        r_gu[threadIdx.x] = gu;
+        r_e2[threadIdx.x] = e2;
+        __syncthreads();
+        for (int h = T / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) {
+                r_gl[threadIdx.x] = fmin(r_gl[threadIdx.x], r_gl[threadIdx.x + h]);
+                r_gu[threadIdx.x] = fmax(r_gu[threadIdx.x], r_gu[threadIdx.x + h]);
+                r_e2[threadIdx.x] = fmax(r_e2[threadIdx.x], r_e2[threadIdx.x + h]);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            root_bounds_finish<Y>(B, r_gl[0], r_gu[0], r_e2[0]);
+            s_gl = r_gl[0];
+            s_gu = r_gu[0];
+        }
+        __syncthreads();
+    }
     if (n == 1) {
         if (threadIdx.x == 0) {
             root_trivial<Y, Lo>(B, wd, reps, reps_lo);
@@ -361,7 +392,7 @@ __global__ void k_rqi(Item* items, const int* list, int w0, int count, const int
                       const BlockDesc* blocks, SolveCfg cfg, Y* scratch, int nmax, DevCounters* C, int pass_iters,
                       int final_pass, int* park_list, int* park_count) {
     constexpr bool kCoop = !std::is_same<Y, dd>::value;
-    __shared__ X tile[kThreads / 32][32][33];
+    __shared__ X tile[kLatThreads / 32][32][33];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // list[w0 .. w0+count) is this launch's share; a later pass is launched
@@ -587,7 +618,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         MRRR_CK(cudaMemcpyAsync(d_blist, blist.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, st));
         // a2: root representations
         tl.begin(MRRR_PHASE_ROOT);
-        k_root<Y, Lo><<<NB, 64, 0, st>>>(d_blist, d_blocks, d_mats, wd, we, reps, reps_lo, cfg);
+        k_root<Y, Lo><<<NB, kRootThreads, 0, st>>>(d_blist, d_blocks, d_mats, wd, we, reps, reps_lo, cfg);
         k_scan_items<<<1, 1024, 0, st>>>(d_blist, NB, d_blocks, d_mats, P, d_total);
         tl.end(2);
         MRRR_CK(cudaGetLastError());
@@ -625,17 +656,17 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 tl.begin(phase);
                 int launches = 0;
                 if (use_low) {
-                    k_bisect_lo_ms<Lo><<<grid_for((long long)count * kMS), kThreads, 0, st>>>(items, list, count,
+                    k_bisect_lo_ms<Lo><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(items, list, count,
                                                                                           d_blocks, wrel_lo, d_C);
-                    k_verify<Y><<<grid_for(2LL * count), kThreads, 0, st>>>(items, list, count, d_blocks, d_C, ctr);
+                    k_verify<Y><<<grid_for(2LL * count, kLatThreads), kLatThreads, 0, st>>>(items, list, count, d_blocks, d_C, ctr);
                     MRRR_CK(cudaMemsetAsync(&d_C->nrefine, 0, sizeof(int), st));
                     k_certify<<<grid_for(count), kThreads, 0, st>>>(items, K, list, count, cfg.gaptol, refine_list,
                                                                     d_C);
-                    k_bisect<Y><<<grid_for(count), kThreads, 0, st>>>(items, refine_list, count, &d_C->nrefine,
+                    k_bisect<Y><<<grid_for(count, kLatThreads), kLatThreads, 0, st>>>(items, refine_list, count, &d_C->nrefine,
                                                                        d_blocks, cfg.rtol_class, 0, ctr);
                     launches = 4;
                 } else {
-                    k_bisect<Y><<<grid_for(count), kThreads, 0, st>>>(items, list, count, nullptr, d_blocks,
+                    k_bisect<Y><<<grid_for(count, kLatThreads), kLatThreads, 0, st>>>(items, list, count, nullptr, d_blocks,
                                                                        cfg.rtol_class, verify_ws ? 1 : 0, ctr);
                     launches = 1;
                 }
@@ -677,7 +708,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                     for (long long w0 = 0; w0 < S; w0 += wave) {
                         int c = (int)std::min<long long>(wave, S - w0);
                         tl.begin(MRRR_PHASE_RQI, rs);
-                        k_rqi<X, Y><<<grid_for(c), kThreads, 0, rs>>>(items, list, (int)w0, c, total, d_mats, d_blocks,
+                        k_rqi<X, Y><<<grid_for(c, kLatThreads), kLatThreads, 0, rs>>>(items, list, (int)w0, c, total, d_mats, d_blocks,
                                                                       cfg, scratch, nmax, d_C, iters,
                                                                       final_pass ? 1 : 0, out, cnt);
                         tl.end(1, rs);
@@ -722,7 +753,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 MRRR_ALLOC(pool, Y, (size_t)C.pool_need);
                 MRRR_ALLOC(pool_lo, Lo, (size_t)C.pool_need / 2);
                 tl.begin(MRRR_PHASE_SHIFT);
-                k_shift<Y, Lo><<<grid_for(C.ncluster), kThreads, 0, st>>>(out, C.ncluster, items, d_blocks, pool,
+                k_shift<Y, Lo><<<grid_for(C.ncluster, kLatThreads), kLatThreads, 0, st>>>(out, C.ncluster, items, d_blocks, pool,
                                                                           pool_lo, cfg, d_C);
                 tl.end();
                 MRRR_CK(cudaGetLastError());
