@@ -221,6 +221,10 @@ __device__ __forceinline__ double solve_twisted_fast(const double* __restrict__ 
                 double z;
                 if (dabsbits(zprev) != 0) {
                     z = -(cur[q] * zprev);
+                } else if (dabsbits(zprev2) == 0) {
+                    // two zeros in a row: the vector has underflowed and stays
+                    // zero from here on (no divide for these rows)
+                    z = 0.0;
                 } else if (down) {
                     // row i+1 with z_{i+1} = 0: e_i z_i + e_{i+1} z_{i+2} = 0
                     z = (i + 2 < n) ? -(__ldg(LD + i + 1) / __ldg(LD + i)) * zprev2 : 0.0;

@@ -424,22 +424,49 @@ MRRR_HD unsigned long long bisect_lo_item(Item& I, double pivmin, double wrel, i
 // Re-establish one end of the bracket in the working precision: side 0 needs
 // negcount(lo) < j, side 1 needs negcount(hi) >= j.  A failing end is moved
 // outward by a doubling step; after 8 failures it jumps to the bound of the
-// whole root spectrum in the item's coordinates.  Returns qd steps; *fails
-// counts the widenings.
+// whole root spectrum in the item's coordinates.  The check is split so a
+// kernel can make the first count for every end and widen only the few that
+// failed, densely packed: endpoint_ok (one count), endpoint_step (the first
+// widening step, from the bracket before any end moved) and widen_endpoint
+// (the loop after a failed first count).
+
 template <class Y>
-MRRR_HD unsigned long long verify_endpoint(Item& I, const BlockDesc& B, int side, int* fails) {
+MRRR_HD int endpoint_count(const Item& I, const BlockDesc& B, int side) {
     const int n = I.n;
-    if (n == 1) return 0;
+    const Y* rep = (const Y*)I.rep;
+    return count_at<Y, true>(rep, rep + 3 * n, n, from_d<Y>(side ? I.hi : I.lo), from_d<Y>(B.pivmin));
+}
+
+MRRR_HD bool endpoint_holds(const Item& I, int side, int c) { return side ? (c >= I.j) : (c < I.j); }
+
+template <class Y>
+MRRR_HD bool endpoint_ok(const Item& I, const BlockDesc& B, int side) {
+    if (I.n == 1) return true;
+    return endpoint_holds(I, side, endpoint_count<Y>(I, B, side));
+}
+
+MRRR_HD double endpoint_step(const Item& I, const BlockDesc& B, int side) {
+    double x = side ? I.hi : I.lo;
+    return fmax(fmax(I.hi - I.lo, 4.0 * Prec<double>::eps * fabs(x)), 4.0 * B.pivmin);
+}
+
+// Returns the new end; *steps += qd steps, *fails += widenings (the failed
+// first count included).
+template <class Y>
+MRRR_HD double widen_endpoint(const Item& I, const BlockDesc& B, int side, double w, unsigned long long* steps,
+                              int* fails) {
+    const int n = I.n;
     const Y* rep = (const Y*)I.rep;
     const Y* D = rep;
     const Y* LLD = rep + 3 * n;
     Y pm = from_d<Y>(B.pivmin);
     double x = side ? I.hi : I.lo;
-    double w = fmax(fmax(I.hi - I.lo, 4.0 * Prec<double>::eps * fabs(x)), 4.0 * B.pivmin);
-    unsigned long long steps = 0;
-    int f = 0;
-    for (int it = 0; it < 64; ++it) {
-        ++steps;
+    int f = 1;
+    x = side ? x + w : x - w;
+    w *= 2.0;
+    unsigned long long st = 0;
+    for (int it = 1; it < 64; ++it) {
+        ++st;
         int c = count_at<Y, true>(D, LLD, n, from_d<Y>(x), pm);
         bool ok = side ? (c >= I.j) : (c < I.j);
         if (ok) break;
@@ -457,10 +484,22 @@ MRRR_HD unsigned long long verify_endpoint(Item& I, const BlockDesc& B, int side
         x = side ? x + w : x - w;
         w *= 2.0;
     }
+    *steps += st * (unsigned long long)n;
+    *fails += f;
+    return x;
+}
+
+// Both steps for one end on one thread.  Returns qd steps; *fails counts
+// the widenings.
+template <class Y>
+MRRR_HD unsigned long long verify_endpoint(Item& I, const BlockDesc& B, int side, int* fails) {
+    if (I.n == 1) return 0;
+    unsigned long long steps = (unsigned long long)I.n;
+    if (endpoint_ok<Y>(I, B, side)) return steps;
+    double x = widen_endpoint<Y>(I, B, side, endpoint_step(I, B, side), &steps, fails);
     if (side) I.hi = x;
     else I.lo = x;
-    *fails += f;
-    return steps * (unsigned long long)n;
+    return steps;
 }
 
 // An item is certified when, for each neighbour in the same rep, the

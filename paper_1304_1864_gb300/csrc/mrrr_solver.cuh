@@ -334,17 +334,164 @@ __global__ void k_bisect_lo_ms(Item* items, const int* list, int count, const Bl
     }
 }
 
-// Two threads per item: one per end of the bracket.
+// Working-precision refinement of the listed items by multisection (the
+// same kMS-point sweeps as k_bisect_lo_ms, with the count of the working
+// precision): down to hi - lo <= max(rtol max(|lo|, |hi|), 2 pivmin), as
+// bisect_bracket.  The refinement starts from verified brackets a few bits
+// wide, so two sweeps replace about five sequential bisection steps, and the
+// kMS lanes per item put four times as many warps on the FP64 pipes.  The
+// list length is read on the device.
+template <class Y>
+__global__ void k_bisect_ms(Item* items, const int* list, const int* count_dev, int bound, const BlockDesc* blocks,
+                            double rtol, unsigned long long* step_counter) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int g = t / kMS, q = t % kMS;
+    if (g >= bound || g >= *count_dev) return;  // whole groups leave together (kMS divides 32)
+    unsigned mask = ((1u << kMS) - 1u) << ((threadIdx.x & 31) & ~(kMS - 1));
+    Item& I = items[list[g]];
+    const int n = I.n;
+    if (n == 1) {
+        if (q == 0) {
+            I.lo = 0.0;
+            I.hi = 0.0;
+        }
+        return;
+    }
+    const Y* D = (const Y*)I.rep;
+    const Y* LLD = D + 3 * n;
+    const double pivmin = blocks[I.block].pivmin;
+    const Y pm = from_d<Y>(pivmin);
+    double lo = I.lo, hi = I.hi;
+    unsigned long long steps = 0;
+    for (int it = 0; it < 64; ++it) {
+        double tol = fmax(rtol * fmax(fabs(lo), fabs(hi)), 2.0 * pivmin);
+        if (!(tol < hi - lo)) break;
+        double w = (hi - lo) / (kMS + 1);
+        double x = lo + w * (q + 1);
+        bool inside = x > lo && x < hi;
+        int c = inside ? count_at<Y, true>(D, LLD, n, from_d<Y>(x), pm) : (q < kMS / 2 ? -1 : n + 1);
+        if (inside) steps += (unsigned long long)n;
+        // first point (left to right) whose count reaches j: new upper end;
+        // the point before it: new lower end
+        double nlo = lo, nhi = hi;
+        bool any_inside = false, found = false;
+#pragma unroll
+        for (int k = 0; k < kMS; ++k) {
+            int ck = __shfl_sync(mask, c, k, kMS);
+            double xk = __shfl_sync(mask, x, k, kMS);
+            bool ik = __shfl_sync(mask, (int)inside, k, kMS) != 0;
+            any_inside |= ik;
+            if (!ik || found) continue;
+            if (ck >= I.j) {
+                nhi = xk;
+                found = true;
+            } else {
+                nlo = xk;
+            }
+        }
+        if (!any_inside) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (q == 0) {
+        I.lo = lo;
+        I.hi = hi;
+    }
+    if (steps) atomicAdd(step_counter, steps);
+}
+
+// Two threads per item, one per end of the bracket: one working-precision
+// count each.  An end that fails marks its item (bit `side` of vflags); the
+// first of the two to mark it appends the item to fix_list, so that the few
+// items whose ends must move run in a separate, densely packed launch
+// instead of holding a whole warp here.
 template <class Y>
 __global__ void k_verify(Item* items, const int* list, int count, const BlockDesc* blocks, DevCounters* C,
-                         unsigned long long* step_counter) {
+                         unsigned long long* step_counter, int* vflags, int* fix_list) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * count) return;
-    Item& I = items[list ? list[t >> 1] : (t >> 1)];
+    int it = list ? list[t >> 1] : (t >> 1);
+    const Item& I = items[it];
+    if (I.n == 1) return;
+    const int side = t & 1;
+    int c = endpoint_count<Y>(I, blocks[I.block], side);
+    atomicAdd(step_counter, (unsigned long long)I.n);
+    if (!endpoint_holds(I, side, c) && atomicOr(&vflags[it], 1 << side) == 0) fix_list[atomicAdd(&C->nvfix, 1)] = it;
+}
+
+// kMS lanes per listed item move its failing ends.  For a failing lower end
+// x (count(x) >= j) the lanes test, in one sweep, the points x - w 4^k for
+// k = 1..kMS (the next sweep continues with k = kMS+1..2 kMS); the point
+// nearest to x whose count is < j is the new lower end, and the point tested
+// just before it -- whose count is still >= j, so it bounds lambda_j from
+// above -- the new upper end when that end did not fail too.  Symmetrically
+// for a failing upper end.  w is the first doubling step of the sequential
+// check (endpoint_step), so one sweep covers eight doublings.  After two
+// sweeps the end falls back to the sequential widening, which ends at the
+// bound of the whole spectrum.
+constexpr int kFixSweeps = 2;
+template <class Y>
+__global__ void k_verify_fix(Item* items, const int* fix_list, int bound, const BlockDesc* blocks, DevCounters* C,
+                             unsigned long long* step_counter, int* vflags) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int g = t / kMS, q = t % kMS;
+    if (g >= bound || g >= C->nvfix) return;  // whole groups leave together (kMS divides 32)
+    unsigned mask = ((1u << kMS) - 1u) << ((threadIdx.x & 31) & ~(kMS - 1));
+    const int it = fix_list[g];
+    Item& I = items[it];
+    const BlockDesc& B = blocks[I.block];
+    const int m = vflags[it];
+    const int n = I.n;
+    const Y* rep = (const Y*)I.rep;
+    const Y pm = from_d<Y>(B.pivmin);
+    const double w0[2] = {endpoint_step(I, B, 0), endpoint_step(I, B, 1)};
+    double x[2] = {I.lo, I.hi};
+    unsigned long long steps = 0;
     int fails = 0;
-    unsigned long long s = verify_endpoint<Y>(I, blocks[I.block], t & 1, &fails);
-    if (s) atomicAdd(step_counter, s);
-    if (fails) atomicAdd(&C->verify_fail, fails);
+    for (int side = 0; side < 2; ++side) {
+        if (!(m & (1 << side))) continue;
+        const double x0 = side ? I.hi : I.lo;
+        double last_fail = x0;  // nearest tested point known to fail
+        bool found = false;
+        double p = x0;
+        for (int sw = 0; sw < kFixSweeps && !found; ++sw) {
+            double f = ldexp(1.0, 2 * (sw * kMS + q + 1));  // 4^(k)
+            double xq = side ? x0 + w0[side] * f : x0 - w0[side] * f;
+            int c = count_at<Y, true>(rep, rep + 3 * n, n, from_d<Y>(xq), pm);
+            steps += (unsigned long long)n;
+            bool ok = endpoint_holds(I, side, c);
+#pragma unroll
+            for (int k = 0; k < kMS; ++k) {
+                bool okk = __shfl_sync(mask, (int)ok, k, kMS) != 0;
+                double xk = __shfl_sync(mask, xq, k, kMS);
+                if (found) continue;
+                if (okk) {
+                    found = true;
+                    p = xk;
+                } else {
+                    last_fail = xk;
+                }
+            }
+        }
+        fails += found ? 1 : 0;
+        if (!found) {
+            // sequential widening from the last failing point
+            Item J = I;
+            if (side) J.hi = last_fail;
+            else J.lo = last_fail;
+            p = widen_endpoint<Y>(J, B, side, w0[side] * ldexp(1.0, 2 * kFixSweeps * kMS), &steps, &fails);
+        }
+        x[side] = p;
+        // the last failing point bounds lambda_j on the other side
+        if (!(m & (1 << (1 - side)))) x[1 - side] = side ? fmax(x[0], last_fail) : fmin(x[1], last_fail);
+    }
+    if (q == 0) {
+        I.lo = x[0];
+        I.hi = x[1];
+        vflags[it] = 0;
+        atomicAdd(&C->verify_fail, fails);
+    }
+    if (steps) atomicAdd(step_counter, steps);
 }
 
 static __global__ void k_certify(const Item* items, int K, const int* list, int count, double gaptol,
@@ -632,6 +779,9 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             MRRR_ALLOC(member_a, int, K);
             MRRR_ALLOC(member_b, int, K);
             MRRR_ALLOC(refine_list, int, K);
+            MRRR_ALLOC(vfix_list, int, K);
+            MRRR_ALLOC(vflags, int, K);
+            MRRR_CK(cudaMemsetAsync(vflags, 0, sizeof(int) * (size_t)K, st));  // each fix launch clears what it used
             MRRR_ALLOC(clus_a, Cluster, K / 2 + 1);
             MRRR_ALLOC(clus_b, Cluster, K / 2 + 1);
             tl.begin(MRRR_PHASE_ROOT);
@@ -658,13 +808,17 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 if (use_low) {
                     k_bisect_lo_ms<Lo><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(items, list, count,
                                                                                           d_blocks, wrel_lo, d_C);
-                    k_verify<Y><<<grid_for(2LL * count, kLatThreads), kLatThreads, 0, st>>>(items, list, count, d_blocks, d_C, ctr);
+                    MRRR_CK(cudaMemsetAsync(&d_C->nvfix, 0, sizeof(int), st));
+                    k_verify<Y><<<grid_for(2LL * count, kLatThreads), kLatThreads, 0, st>>>(
+                        items, list, count, d_blocks, d_C, ctr, vflags, vfix_list);
+                    k_verify_fix<Y><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(
+                        items, vfix_list, count, d_blocks, d_C, ctr, vflags);
                     MRRR_CK(cudaMemsetAsync(&d_C->nrefine, 0, sizeof(int), st));
                     k_certify<<<grid_for(count), kThreads, 0, st>>>(items, K, list, count, cfg.gaptol, refine_list,
                                                                     d_C);
-                    k_bisect<Y><<<grid_for(count, kLatThreads), kLatThreads, 0, st>>>(items, refine_list, count, &d_C->nrefine,
-                                                                       d_blocks, cfg.rtol_class, 0, ctr);
-                    launches = 4;
+                    k_bisect_ms<Y><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(
+                        items, refine_list, &d_C->nrefine, count, d_blocks, cfg.rtol_class, ctr);
+                    launches = 5;
                 } else {
                     k_bisect<Y><<<grid_for(count, kLatThreads), kLatThreads, 0, st>>>(items, list, count, nullptr, d_blocks,
                                                                        cfg.rtol_class, verify_ws ? 1 : 0, ctr);

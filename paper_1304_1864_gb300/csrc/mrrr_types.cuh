@@ -121,6 +121,7 @@ struct DevCounters {
     int reps_relaxed;   // child reps accepted only under the relaxed growth bound of Eq. (3.6)
     int nrefine;        // items needing working-precision refinement at the current step
     int npark;          // eigenpairs parked for the next RQI pass
+    int nvfix;          // items with a bracket end that failed its first check
 };
 
 }  // namespace mrrr
