@@ -2,9 +2,12 @@
 
 Workload (one step): the three n = 4001 tridiagonals of the mixed
 single/double configuration -- 1-2-1 Toeplitz, Wilkinson W_4001 and Clement --
-float32 in/out with binary64 internals, all eigenpairs, each matrix an
-independent problem, solved in one batched call.  Inputs are resident on the
-device; L2 is flushed (256 MiB write) between timed steps.
+float32 in/out with binary64 internals, all eigenpairs, each matrix solved on
+its own by one mrrr_solve_s call (the three calls run concurrently on three
+streams).  Inputs are resident on the device; L2 is flushed (256 MiB write)
+between timed steps.  Also reported: the same step as sequential solves and
+as one batched call, the 4096-matrix batched workload, the double-double
+glued-Wilkinson solve and a bounded replay of the serving trace.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank solves its own copy of the workload (weak scaling,
@@ -95,6 +98,11 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _log(msg):
+    sys.stderr.write("[bench %s] %s\n" % (time.strftime("%H:%M:%S"), msg))
+    sys.stderr.flush()
 
 
 def _dist():
@@ -203,6 +211,78 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+def _concurrent(fns):
+    """Run the callables on their own host threads (the C ABI releases the
+    interpreter lock) and re-raise the first failure."""
+    errs = []
+
+    def wrap(f):
+        try:
+            f()
+        except BaseException as ex:  # noqa: BLE001 - reported below
+            errs.append(ex)
+
+    ts = [threading.Thread(target=wrap, args=(f,)) for f in fns]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if errs:
+        raise errs[0]
+
+
+class _Solo:
+    """The C2 step: each matrix solved on its own by one mrrr_solve_s call,
+    the three calls issued concurrently on three CUDA streams from three host
+    threads, ordered after / before the caller's stream."""
+
+    def __init__(self, m, mats, dev):
+        import torch
+        self.m, self.mats, self.dev = m, mats, dev
+        self.streams = [torch.cuda.Stream(dev) for _ in mats]
+        self.stats = [None] * len(mats)
+
+    def run(self, timing=False):
+        import torch
+        main = torch.cuda.current_stream(self.dev)
+        for s in self.streams:
+            s.wait_stream(main)
+
+        def one(i):
+            d, e = self.mats[i]
+            with torch.cuda.stream(self.streams[i]):
+                W, Z, st = self.m.solve(d, e, mode="mixed", timing=timing, check=False)
+            assert st["status"] == 0, st["status"]
+            self.stats[i] = st
+
+        _concurrent([lambda i=i: one(i) for i in range(len(self.mats))])
+        for s in self.streams:
+            main.wait_stream(s)
+        return [dict(st) for st in self.stats]
+
+
+def _time_steps(fn, steps, dev, flush):
+    """Device time (ms) of `steps` calls of fn(), an L2 flush before each;
+    returns (total ms, results)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    total = 0.0
+    out = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out.append(fn())
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    return total, out
+
+
+PHASES_L = ("prep", "root", "bisect", "classify", "shift", "refine", "rqi", "finish")
+
+
 def run_ours(args):
     import torch
     rank, world, local = _dist()
@@ -218,69 +298,72 @@ def run_ours(args):
     mats = [(torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev)) for d, e in mats_h]
     pairs_per_step = sum(d.shape[0] for d, _ in mats_h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    solo = _Solo(m, mats, dev)
     for _ in range(args.warmup):
-        m.solve_batch(mats, mode="mixed")
+        solo.run()
     torch.cuda.synchronize(dev)
     _barrier(world)
-    stats_acc = {}
-    launches = 0
-    ms_total = 0.0
     with ClockSampler(dev.index) as clk:
         torch.cuda.synchronize(dev)
         _barrier(world)
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            out, st, status = m.solve_batch(mats, mode="mixed", timing=True)
-            b.record(stream)
-            b.synchronize()
-            assert all(s == 0 for s in status), status
-            ms_total += a.elapsed_time(b)
-            launches += sum(st["phase_launches"].values())
-            for k, v in st["phase_ms"].items():
-                stats_acc.setdefault("ms_" + k, 0.0)
-                stats_acc["ms_" + k] += v
-            for k in ("qd_bisect", "qd_refine", "qd_rqi", "qd_shift"):
-                stats_acc[k] = stats_acc.get(k, 0) + st[k]
-            last_stats = st
+        ms_total, outs = _time_steps(lambda: solo.run(timing=True), args.steps, dev, flush)
         torch.cuda.synchronize(dev)
         _barrier(world)
+    acc = {}
+    launches = 0
+    for sts in outs:
+        for st in sts:
+            launches += sum(st["phase_launches"].values())
+            for k in PHASES_L:
+                acc["ms_" + k] = acc.get("ms_" + k, 0.0) + st["phase_ms"][k]
+                acc["n_" + k] = acc.get("n_" + k, 0) + st["phase_launches"][k]
+            for k in ("qd_bisect", "qd_refine", "qd_rqi", "qd_shift"):
+                acc[k] = acc.get(k, 0) + st[k]
+    last = outs[-1]
     ms_max = _max_over_ranks(ms_total, world, dev)
     value = pairs_per_step * args.steps * world / (ms_max / 1e3)
-    # dominant kernel and its roofline (FP64 ALU bound)
-    phase_ms = {k[3:]: v for k, v in stats_acc.items() if k.startswith("ms_")}
+    # dominant kernel and its roofline (FP64 ALU bound); every launch is timed
+    # with CUDA events on the stream it runs on
+    phase_ms = {k: acc["ms_" + k] for k in PHASES_L}
     dom = max(PHASE_COUNTER, key=lambda p: phase_ms.get(p, 0.0))
-    flops = stats_acc[PHASE_COUNTER[dom]] * FLOPS_PER_STEP[dom]
-    launches_dom = last_stats["phase_launches"][dom] * args.steps
+    flops = acc[PHASE_COUNTER[dom]] * FLOPS_PER_STEP[dom]
+    launches_dom = acc["n_" + dom]
     achieved = flops / (phase_ms[dom] / 1e3) / 1e9 if phase_ms[dom] > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None, "kernel": PHASE_KERNEL[dom],
                 "phase": dom, "launches": launches_dom,
                 "ms_per_launch": phase_ms[dom] / max(launches_dom, 1),
                 "flops_per_launch": flops / max(launches_dom, 1),
-                "peak_note": "FP64 FMA peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
+                "peak_note": "of derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (the measured "
+                             "peaks file has no FP64 figure; a DFMA loop measured 1194 GFLOP/s)",
                 "phase_share": {k: v / max(sum(phase_ms.values()), 1e-30) for k, v in phase_ms.items()}}
-    # end to end: the public C ABI with pinned host buffers, copies inside the timed region
-    e2e = None
-    if rank == 0:
-        e2e = _e2e(m, mats_h, args, dev)
     line = None
     if rank == 0:
+        _log("timed steps: %.1f ms" % ms_total)
+        e2e = _e2e(m, mats_h, args, dev)
+        _log("e2e done")
         cb = cpu_baseline(mats_h) if (world == 1 and not args.no_cpu_baseline) else None
+        _log("cpu baseline done")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "mode": "mixed single/double (fp32 io, fp64 internals)",
+                           "solves": "each matrix solved on its own: 3 mrrr_solve_s calls issued concurrently "
+                                     "on 3 CUDA streams from 3 host threads",
                            "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replica per GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "tree": {"d_max": last_stats["d_max"], "clusters": last_stats["nclusters"],
-                                                  "largest_cluster": last_stats["largest_cluster"],
-                                                  "reps_failed": last_stats["reps_failed"],
-                                                  "rqi_iters": last_stats["rqi_iters"],
-                                                  "fallbacks": last_stats["fallbacks"]}}
+                "clocks": clk.summary(),
+                "tree": {nm: [st[key] for st in last] for nm, key in
+                         (("d_max", "d_max"), ("clusters", "nclusters"), ("largest_cluster", "largest_cluster"),
+                          ("reps_failed", "reps_failed"), ("rqi_iters", "rqi_iters"), ("fallbacks", "fallbacks"))}}
+        line["variants"] = _variants(m, mats, args, dev, flush)
+        if not args.no_extras:
+            for key, fn in (("c4_batched", lambda: _c4(m, dev, flush)),
+                            ("c3_dd", lambda: _c3(m, dev, flush)),
+                            ("serve", lambda: _serve(m, dev, args.serve_requests))):
+                t0 = time.perf_counter()
+                line[key] = fn()
+                _log("%s: %.1f s" % (key, time.perf_counter() - t0))
         if args.plain:
             line["plain"] = _plain(m, mats, args, dev)
         print(json.dumps(line), flush=True)
@@ -288,6 +371,126 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _variants(m, mats, args, dev, flush):
+    """The same C2 step issued as three sequential solves and as one batched
+    call (mrrr_solve_batch_s)."""
+    import torch
+    pairs = sum(d.shape[0] for d, _ in mats)
+    res = {}
+
+    def seq():
+        for d, e in mats:
+            m.solve(d, e, mode="mixed", check=True)
+
+    def bat():
+        out, st, status = m.solve_batch(mats, mode="mixed")
+        assert all(s == 0 for s in status), status
+
+    for label, fn in (("sequential_solves", seq), ("one_batched_call", bat)):
+        fn()
+        torch.cuda.synchronize(dev)
+        ms, _ = _time_steps(fn, args.steps, dev, flush)
+        res[label] = {"value": pairs * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps}
+    return res
+
+
+def _c4(m, dev, flush):
+    """Batched workload: 4096 tridiagonals, n log-uniform in [32, 2048], types
+    {U(-1,1), 1-2-1, Wilkinson, glued W_21 (coupling 1e-8)}, fp32 in, fp64
+    internals, all eigenpairs, one mrrr_solve_batch_s call; one warm-up call
+    and one timed call."""
+    import torch
+    from paper_1304_1864_gb300 import inputs
+    batch = inputs.workload_c4(count=4096, seed=4)
+    mats = [(torch.tensor(d, dtype=torch.float32, device=dev), torch.tensor(e, dtype=torch.float32, device=dev))
+            for _, d, e in batch]
+    pairs = sum(d.size for _, d, _ in batch)
+
+    def step():
+        out, st, status = m.solve_batch(mats, mode="mixed")
+        assert all(s == 0 for s in status)
+        return st
+
+    step()
+    torch.cuda.synchronize(dev)
+    ms, sts = _time_steps(step, 1, dev, flush)
+    st = sts[0]
+    return {"value": pairs / (ms / 1e3), "unit": UNIT, "ms": ms, "matrices": len(batch), "eigenpairs": pairs,
+            "d_max": st["d_max"], "clusters": st["nclusters"], "fallbacks": st["fallbacks"],
+            "workload": "4096 tridiagonals, n log-uniform [32, 2048], seed 4, types uniform/1-2-1/Wilkinson/"
+                        "glued W_21, fp32 in, fp64 internals, all pairs, one batched call"}
+
+
+def _c3(m, dev, flush):
+    """Glued Wilkinson, 40 x W_201 with couplings 1e-8 (n = 8040), fp64 in,
+    double-double internals, all eigenpairs; one warm-up and one timed solve."""
+    import torch
+    from paper_1304_1864_gb300 import inputs
+    (d, e), = inputs.workload_c3()
+    dd = torch.tensor(d, dtype=torch.float64, device=dev)
+    ee = torch.tensor(e, dtype=torch.float64, device=dev)
+    m.solve(dd, ee, mode="mixed")
+    torch.cuda.synchronize(dev)
+    ms, sts = _time_steps(lambda: m.solve(dd, ee, mode="mixed")[2], 1, dev, flush)
+    st = sts[0]
+    return {"value": d.size / (ms / 1e3), "unit": UNIT, "ms": ms, "n": int(d.size), "d_max": st["d_max"],
+            "clusters": st["nclusters"], "largest_cluster": st["largest_cluster"],
+            "workload": "glued Wilkinson 40 x W_201, couplings 1e-8, n=8040, fp64 in, double-double internals"}
+
+
+def _serve(m, dev, count):
+    """Serving loop: the first `count` requests of the seeded Poisson trace
+    (2000 requests/s, n log-uniform [64, 16384], half fp32 in with fp64
+    internals, half fp64 in with double-double internals, half all pairs, half
+    a random contiguous 10% index range), submitted at their arrival times
+    (host inputs, device outputs) to one server; latency is submit to
+    completion."""
+    import torch
+    from paper_1304_1864_gb300 import inputs
+    trace = inputs.serving_trace(rate=2000.0, seconds=1.0, seed=5)[:count]
+    reqs = []
+    for r in trace:
+        d, e = inputs.make(r["kind"], r["n"], seed=int(r["t"] * 1e6) % (2**31))
+        n = d.size
+        if r["il"] == 1 and r["iu"] == r["n"]:
+            il, iu = 0, 0
+        else:
+            il = min(r["il"], n)
+            iu = max(il, min(r["iu"], n))
+        npdt = np.float32 if r["prec"] == "s" else np.float64
+        reqs.append((r["t"], d.astype(npdt), (e if n > 1 else np.zeros(1)).astype(npdt), il, iu, r["prec"]))
+    srv = m.Server(workers=3)
+    try:
+        keep = {}
+        t0 = time.perf_counter()
+        for t, d, e, il, iu, prec in reqs:
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            n = d.size
+            k = (iu - il + 1) if il else n
+            tdt = torch.float32 if prec == "s" else torch.float64
+            W = torch.empty(k, dtype=tdt, device=dev)
+            Z = torch.empty((k, n), dtype=tdt, device=dev)
+            tk = srv.submit(d, e, W, Z, mode="mixed", il=il, iu=iu)
+            keep[tk] = (W, Z)
+        bad = 0
+        for tk in list(keep):
+            rc, info = srv.poll(tk, wait_ms=-1)
+            bad += rc != 0
+            del keep[tk]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"requests": len(reqs), "failed": bad, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "max_ms": st["max_ms"], "eigenpairs": st["eigenpairs"], "batches": st["batches"],
+            "value": st["eigenpairs"] / max(st["busy_s"], 1e-9), "unit": UNIT, "wall_s": wall,
+            "offered": "Poisson 2000 requests/s (trace seed 5), first %d requests replayed at their arrival times; "
+                       "n log-uniform [64, 16384]; half fp32->fp64, half fp64->double-double; half all pairs, "
+                       "half 10%% index ranges; 3 workers, budget = half the free HBM" % len(reqs)}
 
 
 def _plain(m, mats, args, dev):
@@ -314,6 +517,10 @@ def _plain(m, mats, args, dev):
 
 
 def _e2e(m, mats_h, args, dev):
+    """The C2 step through the public C ABI with pinned host buffers: three
+    mrrr_solve_s calls (one per matrix) issued concurrently from three host
+    threads on three streams; each call copies its inputs in and its W and Z
+    out inside the timed region."""
     import ctypes
     import torch
     pin = []
@@ -323,17 +530,18 @@ def _e2e(m, mats_h, args, dev):
         ep = torch.from_numpy(e).pin_memory()
         W = torch.empty(n, dtype=torch.float32).pin_memory()
         Z = torch.empty((n, n), dtype=torch.float32).pin_memory()
-        pin.append((n, dp, ep, W, Z))
-    stream = torch.cuda.current_stream(dev)
-    sh = ctypes.c_void_p(stream.cuda_stream)
+        pin.append((n, dp, ep, W, Z, torch.cuda.Stream(dev)))
+
+    def one(n, dp, ep, W, Z, s):
+        mcount = ctypes.c_int(0)
+        rc = m.mrrr_solve_s(n, ctypes.c_void_p(dp.data_ptr()), ctypes.c_void_p(ep.data_ptr()), 0,
+                            ctypes.c_float(0), ctypes.c_float(0), 1, n, 1, None, ctypes.byref(mcount),
+                            ctypes.c_void_p(W.data_ptr()), ctypes.c_void_p(Z.data_ptr()), n,
+                            ctypes.c_void_p(s.cuda_stream))
+        assert rc == 0, rc
 
     def step():
-        for n, dp, ep, W, Z in pin:
-            mcount = ctypes.c_int(0)
-            rc = m.mrrr_solve_s(n, ctypes.c_void_p(dp.data_ptr()), ctypes.c_void_p(ep.data_ptr()), 0,
-                                ctypes.c_float(0), ctypes.c_float(0), 1, n, 1, None, ctypes.byref(mcount),
-                                ctypes.c_void_p(W.data_ptr()), ctypes.c_void_p(Z.data_ptr()), n, sh)
-            assert rc == 0, rc
+        _concurrent([lambda p=p: one(*p) for p in pin])
 
     for _ in range(max(1, args.warmup)):
         step()
@@ -345,7 +553,7 @@ def _e2e(m, mats_h, args, dev):
     h2d = sum(4 * (2 * p[0] - 1) for p in pin)
     d2h = sum(4 * (p[0] + p[0] * p[0]) for p in pin)
     return {"value": pairs * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "api": "mrrr_solve_s x3 with pinned host buffers (sequential calls)"}
+            "api": "mrrr_solve_s x3 with pinned host buffers, one call per matrix, concurrent on 3 streams"}
 
 
 def main():
@@ -356,6 +564,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain", action="store_true", help="also time the plain (y = x) solvers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, C3, C4 and serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests replayed from the serving trace")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

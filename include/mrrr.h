@@ -194,6 +194,86 @@ int mrrr_solve_batch_d(int nb, const int* n, const double* const* d, const doubl
 int mrrr_eigvecs_noalloc_s(int n, const float* d, const float* e, int il, int k, const float* W, float* Z,
                            int ldz, void* stream);
 
+/*
+ * Serving loop: continuous batching of independent solve requests.
+ *
+ * The paper solves one matrix at a time; this is the request loop around the
+ * same solver for many clients.  A server owns `workers` host threads, each
+ * with its own CUDA stream.  Submitted requests wait in arrival order; a free
+ * worker admits the oldest pending request and every later pending request
+ * of the same precision and mode, as long as the device bytes charged to the
+ * admitted requests stay within `hbm_budget` (a request is charged its
+ * device inputs, device copies of host outputs and the solver's own
+ * representation, item and RQI scratch; a request larger than the whole
+ * budget runs alone once nothing else is admitted), and runs them as one
+ * batched solve (mrrr_solve_batch_s / _d semantics, each matrix solved on its
+ * own, so a result does not depend on what it was batched with).  Requests
+ * that arrive while batches run are admitted by the next worker that frees
+ * up, so work from different batches overlaps on the device.
+ *
+ * Ownership: the caller owns the output buffers named in the request (host
+ * or device; host outputs are written by a device-to-host copy when the
+ * batch completes) and must keep them, and device inputs, alive until the
+ * request is polled complete.  Host inputs are copied at submit.  Device
+ * buffers are used only after the work the caller queued on the request's
+ * stream before submit (an event recorded at submit).  Every call
+ * is thread-safe.  A server is bound to the device current at open.
+ */
+typedef struct mrrr_server mrrr_server;
+
+typedef struct {
+    int workers;          /* concurrent batches (host threads + streams) [2] */
+    int max_batch;        /* requests per batch [512] */
+    long long hbm_budget; /* device bytes for admitted requests; 0: half the free memory at open */
+} mrrr_serve_config;
+
+typedef struct {
+    int precision;   /* 0: binary32 I/O (as mrrr_solve_s), 1: binary64 I/O (as mrrr_solve_d) */
+    mrrr_mode mode;  /* MRRR_MIXED or MRRR_PLAIN */
+    int n;           /* order, >= 1 */
+    const void* d;   /* diagonal, n values of the request's precision (host or device) */
+    const void* e;   /* off-diagonal, n - 1 values (may be NULL when n = 1) */
+    int il, iu;      /* 1-based index range; il = 0 selects all eigenpairs */
+    void* W;         /* output eigenvalues, >= iu - il + 1 (or n) values (host or device) */
+    void* Z;         /* output eigenvectors, column-major, leading dimension ldz >= n */
+    int ldz;
+    void* stream;    /* device buffers are ready once the work queued on this cudaStream_t before
+                        submit has run (NULL: the legacy default stream); completion is reported by
+                        mrrr_serve_poll, not ordered on this stream */
+} mrrr_request;
+
+typedef struct {
+    int status;        /* the request's own status (0 or a negative MRRR_ERR_*) */
+    int m;             /* eigenpairs returned */
+    int batch;         /* requests in the batch it ran in */
+    double queue_ms;   /* submit to admission */
+    double latency_ms; /* submit to completion (outputs written) */
+} mrrr_serve_info;
+
+typedef struct {
+    long long completed;  /* requests completed since open */
+    long long eigenpairs; /* eigenpairs returned by them */
+    long long batches;    /* batched solves run */
+    double p50_ms, p99_ms, max_ms; /* latency percentiles over the completed requests */
+    double busy_s;        /* wall time from the first admission to the last completion */
+} mrrr_serve_stats;
+
+#define MRRR_PENDING 1  /* mrrr_serve_poll: not complete yet */
+
+/* Start a server (cfg may be NULL for the defaults). */
+int mrrr_serve_open(const mrrr_serve_config* cfg, mrrr_server** out);
+/* Queue a request; *ticket identifies it for mrrr_serve_poll.  Argument
+   errors are reported here, before anything is queued. */
+int mrrr_serve_submit(mrrr_server* s, const mrrr_request* req, long long* ticket);
+/* Wait up to wait_ms (< 0: no limit) for the request.  Returns MRRR_PENDING
+   if it is not complete, else its status, fills *info (may be NULL) and
+   retires the ticket.  An unknown ticket returns MRRR_ERR_ARG. */
+int mrrr_serve_poll(mrrr_server* s, long long ticket, int wait_ms, mrrr_serve_info* info);
+/* Latency and throughput counters since open. */
+int mrrr_serve_stats_get(mrrr_server* s, mrrr_serve_stats* out);
+/* Finish every queued request, stop the workers and free the server. */
+int mrrr_serve_close(mrrr_server* s);
+
 /* Human-readable text for a status code (static storage). */
 const char* mrrr_strerror(int status);
 

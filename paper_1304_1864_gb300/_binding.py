@@ -44,6 +44,34 @@ class MrrrParams(ctypes.Structure):
                 ("flags", ctypes.c_int), ("stats", ctypes.POINTER(MrrrStats))]
 
 
+MRRR_PENDING = 1
+
+
+class MrrrServeConfig(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int), ("max_batch", ctypes.c_int), ("hbm_budget", ctypes.c_longlong)]
+
+
+class MrrrRequest(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("n", ctypes.c_int),
+                ("d", ctypes.c_void_p), ("e", ctypes.c_void_p), ("il", ctypes.c_int), ("iu", ctypes.c_int),
+                ("W", ctypes.c_void_p), ("Z", ctypes.c_void_p), ("ldz", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class MrrrServeInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("m", ctypes.c_int), ("batch", ctypes.c_int),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class MrrrServeStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_longlong), ("eigenpairs", ctypes.c_longlong), ("batches", ctypes.c_longlong),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("busy_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class MrrrError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
@@ -73,6 +101,14 @@ def lib():
         L.mrrr_eigvecs_noalloc_s.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
                                              vp]
         L.mrrr_eigvecs_noalloc_s.restype = ctypes.c_int
+        L.mrrr_serve_open.argtypes = [ctypes.POINTER(MrrrServeConfig), ctypes.POINTER(ctypes.c_void_p)]
+        L.mrrr_serve_submit.argtypes = [vp, ctypes.POINTER(MrrrRequest), ctypes.POINTER(ctypes.c_longlong)]
+        L.mrrr_serve_poll.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(MrrrServeInfo)]
+        L.mrrr_serve_stats_get.argtypes = [vp, ctypes.POINTER(MrrrServeStats)]
+        L.mrrr_serve_close.argtypes = [vp]
+        for name in ("mrrr_serve_open", "mrrr_serve_submit", "mrrr_serve_poll", "mrrr_serve_stats_get",
+                     "mrrr_serve_close"):
+            getattr(L, name).restype = ctypes.c_int
         L.mrrr_strerror.argtypes = [ctypes.c_int]
         L.mrrr_strerror.restype = ctypes.c_char_p
         L.mrrr_version.argtypes = []
@@ -108,6 +144,26 @@ def mrrr_solve_batch_d(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, stat
 
 def mrrr_eigvecs_noalloc_s(n, d, e, il, k, W, Z, ldz, stream):
     return lib().mrrr_eigvecs_noalloc_s(n, d, e, il, k, W, Z, ldz, stream)
+
+
+def mrrr_serve_open(cfg, out):
+    return lib().mrrr_serve_open(cfg, out)
+
+
+def mrrr_serve_submit(server, req, ticket):
+    return lib().mrrr_serve_submit(server, req, ticket)
+
+
+def mrrr_serve_poll(server, ticket, wait_ms, info):
+    return lib().mrrr_serve_poll(server, ticket, wait_ms, info)
+
+
+def mrrr_serve_stats_get(server, out):
+    return lib().mrrr_serve_stats_get(server, out)
+
+
+def mrrr_serve_close(server):
+    return lib().mrrr_serve_close(server)
 
 
 def mrrr_strerror(code):
@@ -230,3 +286,62 @@ def solve_batch(mats, mode="mixed", ranges=None, stream=None, timing=False, chec
         raise MrrrError(rc, "mrrr_solve_batch")
     out = [(Ws[i][:mout[i]], Zts[i][:mout[i]].T) for i in range(nb)]
     return out, stats.as_dict() | {"status": rc}, list(status)
+
+
+class Server:
+    """The serving loop (mrrr_serve_*).  submit() takes numpy or torch arrays
+    for d and e and the output arrays W (>= k values) and Z (k x n, i.e. the
+    column-major n x k result, row-major in Python); the arrays are kept
+    referenced until the ticket is polled.  poll() returns (status, info dict)
+    or None while the request is pending."""
+
+    def __init__(self, workers=0, max_batch=0, hbm_budget=0):
+        self._h = ctypes.c_void_p()
+        cfg = MrrrServeConfig(workers, max_batch, hbm_budget)
+        rc = lib().mrrr_serve_open(ctypes.byref(cfg), ctypes.byref(self._h))
+        if rc != MRRR_OK:
+            raise MrrrError(rc, "mrrr_serve_open")
+        self._keep = {}
+
+    def submit(self, d, e, W, Z, mode="mixed", il=0, iu=0, stream=None):
+        n = int(d.shape[0])
+        prec = 0 if str(d.dtype).endswith("float32") else 1
+        on_dev = any(_is_torch(x) and x.is_cuda for x in (d, W))
+        req = MrrrRequest(prec, MRRR_MIXED if mode == "mixed" else MRRR_PLAIN, n, _ptr(d),
+                          _ptr(e) if n > 1 else None, il, iu, _ptr(W), _ptr(Z), n,
+                          _stream_handle(stream, on_dev) if on_dev else None)
+        t = ctypes.c_longlong(0)
+        rc = lib().mrrr_serve_submit(self._h, ctypes.byref(req), ctypes.byref(t))
+        if rc != MRRR_OK:
+            raise MrrrError(rc, "mrrr_serve_submit")
+        self._keep[t.value] = (d, e, W, Z)
+        return t.value
+
+    def poll(self, ticket, wait_ms=-1):
+        info = MrrrServeInfo()
+        rc = lib().mrrr_serve_poll(self._h, ticket, wait_ms, ctypes.byref(info))
+        if rc == MRRR_PENDING:
+            return None
+        if rc == MRRR_ERR_ARG and ticket not in self._keep:
+            raise MrrrError(rc, "mrrr_serve_poll")
+        self._keep.pop(ticket, None)
+        return rc, {f: getattr(info, f) for f, _ in info._fields_}
+
+    def stats(self):
+        st = MrrrServeStats()
+        rc = lib().mrrr_serve_stats_get(self._h, ctypes.byref(st))
+        if rc != MRRR_OK:
+            raise MrrrError(rc, "mrrr_serve_stats_get")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().mrrr_serve_close(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

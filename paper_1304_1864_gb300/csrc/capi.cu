@@ -2,6 +2,8 @@
 // defaults, dispatch to the per-precision solvers.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -14,6 +16,62 @@ namespace {
 
 using mrrr::MatrixDesc;
 using mrrr::SolveCfg;
+
+// ---------------------------------------------------------------- memory pool
+
+}  // namespace
+
+namespace mrrr {
+
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64];
+bool g_pool_ok[64];
+
+cudaMemPool_t pool_for_current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_ok[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ULL;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+        g_pool_ok[dev] = true;
+    }
+    return g_pool[dev];
+}
+}  // namespace
+
+void* dev_alloc(size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = pool_for_current_device();
+    void* p = nullptr;
+    if (!pool || cudaMallocFromPoolAsync(&p, bytes ? bytes : 1, pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+}  // namespace mrrr
+
+namespace {
 
 bool on_device(const void* p) {
     if (!p) return false;
@@ -57,9 +115,9 @@ struct DevBuf {
     void* p = nullptr;
     cudaStream_t st;
     explicit DevBuf(cudaStream_t s) : st(s) {}
-    bool alloc(size_t bytes) { return cudaMallocAsync(&p, bytes ? bytes : 1, st) == cudaSuccess; }
+    bool alloc(size_t bytes) { return (p = mrrr::dev_alloc(bytes, st)) != nullptr; }
     ~DevBuf() {
-        if (p) cudaFreeAsync(p, st);
+        mrrr::dev_free(p, st);
     }
 };
 
@@ -195,7 +253,7 @@ int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const
         M.iu = il ? iu[p] : n[p];
         if (n[p] == 1 || !M.e) {
             if (!dzero) {
-                if (cudaMallocAsync((void**)&dzero, sizeof(X), st) != cudaSuccess) return MRRR_ERR_NOMEM;
+                if (!(dzero = (X*)mrrr::dev_alloc(sizeof(X), st))) return MRRR_ERR_NOMEM;
                 if (cudaMemcpyAsync(dzero, zero1, sizeof(X), cudaMemcpyHostToDevice, st) != cudaSuccess)
                     return MRRR_ERR_CUDA;
             }
@@ -226,7 +284,7 @@ int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const
             if (m_out) m_out[p] = mats[q].kout;
         }
     }
-    if (dzero) cudaFreeAsync(dzero, st);
+    mrrr::dev_free(dzero, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return MRRR_ERR_CUDA;
     if (rc != MRRR_OK && rc != MRRR_ERR_NOCONV) return rc;
     for (int p = 0; p < nb; ++p)

@@ -7,6 +7,13 @@
 #include "mrrr_types.cuh"
 
 namespace mrrr {
+// Stream-ordered device memory of the library: one memory pool per device,
+// created on first use, that keeps freed blocks cached for the next solve
+// (release threshold: no limit) instead of returning them to the driver at
+// every synchronisation.  alloc returns nullptr on failure.
+void* dev_alloc(size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+
 // binary32 input/output: working precision binary64 (mixed) or binary32 (plain)
 int solve_batch_s_mixed(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
                         mrrr_stats* stats);

@@ -953,27 +953,4 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     return true;
 }
 
-// --------------------------------------------------------------- ordering of W
-
-// W must be ascending.  Eigenvalues of different blocks were placed by their
-// bracket midpoints; the final values can swap neighbours that lie within
-// rounding of each other.  Repair by insertion with column swaps.
-template <class X>
-MRRR_HD void sort_fix_matrix(MatrixDesc& M) {
-    X* W = (X*)M.W;
-    X* Z = (X*)M.Z;
-    for (int i = 1; i < M.kout; ++i) {
-        int j = i;
-        while (j > 0 && W[j] < W[j - 1]) {
-            X t = W[j]; W[j] = W[j - 1]; W[j - 1] = t;
-            X* c0 = Z + (size_t)j * M.ldz;
-            X* c1 = Z + (size_t)(j - 1) * M.ldz;
-            for (int r = 0; r < M.n; ++r) {
-                X v = c0[r]; c0[r] = c1[r]; c1[r] = v;
-            }
-            --j;
-        }
-    }
-}
-
 }  // namespace mrrr

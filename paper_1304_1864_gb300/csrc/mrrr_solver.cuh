@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "mrrr.h"
+#include "mrrr_entry.h"
 #include "mrrr_phases.cuh"
 
 namespace mrrr {
@@ -596,34 +597,93 @@ __global__ void k_rqi(Item* items, const int* list, int w0, int count, const int
     }
 }
 
+// Ordering of W for matrices that split.  Eigenvalues of different blocks
+// were given their columns by bracket midpoints; the final values can order
+// differently where they agree to rounding (identical blocks give ties).
+// k_rank: the position of each eigenvalue in ascending order, stable (equal
+// values keep their column order, NaN sorts last), by counting, one thread
+// per eigenvalue with the values staged through shared memory in tiles;
+// flag[y] is set when the matrix is not in order yet.  Then k_gather moves
+// column i to column rank(i) of a temporary and k_copy_back copies it back.
+constexpr int kRankTile = 256;
 template <class X>
-__global__ void k_sort_fix(MatrixDesc* mats, int nmat) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nmat) return;
-    if (mats[p].nblocks > 1) sort_fix_matrix<X>(mats[p]);
+__global__ void k_rank(const MatrixDesc* mats, const int* list, const long long* roff, int* rank, int* flag) {
+    __shared__ X tile[kRankTile];
+    const MatrixDesc& M = mats[list[blockIdx.y]];
+    const int k = M.kout;
+    const int i = blockIdx.x * kRankTile + threadIdx.x;
+    if (blockIdx.x * kRankTile >= k) return;  // whole CTA leaves together
+    const X* W = (const X*)M.W;
+    const X wi = i < k ? W[i] : X(0);
+    const bool ni = !(wi == wi);
+    int r = 0;
+    for (int j0 = 0; j0 < k; j0 += kRankTile) {
+        __syncthreads();
+        if (j0 + threadIdx.x < k) tile[threadIdx.x] = W[j0 + threadIdx.x];
+        __syncthreads();
+        const int jn = min(kRankTile, k - j0);
+        if (i < k) {
+            for (int q = 0; q < jn; ++q) {
+                const X wj = tile[q];
+                const int j = j0 + q;
+                const bool nj = !(wj == wj);
+                r += ni ? (!nj || j < i) : (!nj && (wj < wi || (wj == wi && j < i)));
+            }
+        }
+    }
+    if (i < k) {
+        rank[roff[blockIdx.y] + i] = r;
+        if (r != i) flag[blockIdx.y] = 1;
+    }
+}
+
+// CTA (x = column, y = listed matrix): column x of Z (and W[x]) to column
+// rank(x) of the temporary T (leading dimension n) and Wt.
+template <class X>
+__global__ void k_gather(const MatrixDesc* mats, const int* list, const long long* roff, const int* rank,
+                         const long long* toff, X* T, X* Wt) {
+    const MatrixDesc& M = mats[list[blockIdx.y]];
+    const int c = blockIdx.x;
+    if (c >= M.kout) return;
+    const int dst = rank[roff[blockIdx.y] + c];
+    const X* src = (const X*)M.Z + (size_t)c * M.ldz;
+    X* out = T + toff[blockIdx.y] + (size_t)dst * M.n;
+    for (int r = threadIdx.x; r < M.n; r += blockDim.x) out[r] = src[r];
+    if (threadIdx.x == 0) Wt[roff[blockIdx.y] + dst] = ((const X*)M.W)[c];
+}
+
+template <class X>
+__global__ void k_copy_back(const MatrixDesc* mats, const int* list, const long long* roff, const long long* toff,
+                            const X* T, const X* Wt) {
+    const MatrixDesc& M = mats[list[blockIdx.y]];
+    const int c = blockIdx.x;
+    if (c >= M.kout) return;
+    X* dst = (X*)M.Z + (size_t)c * M.ldz;
+    const X* src = T + toff[blockIdx.y] + (size_t)c * M.n;
+    for (int r = threadIdx.x; r < M.n; r += blockDim.x) dst[r] = src[r];
+    if (threadIdx.x == 0) ((X*)M.W)[c] = Wt[roff[blockIdx.y] + c];
 }
 
 // ------------------------------------------------------------------ host driver
 
-// Stream-ordered allocations released together at the end of a solve.
+// Stream-ordered allocations from the library's pool, released together at
+// the end of a solve.
 struct Arena {
     cudaStream_t st;
     std::vector<void*> ptrs;
     bool failed = false;
     explicit Arena(cudaStream_t s) : st(s) {}
     template <class T> T* alloc(size_t count) {
-        void* p = nullptr;
-        size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        void* p = dev_alloc(std::max<size_t>(count, 1) * sizeof(T), st);
+        if (!p) {
             failed = true;
-            cudaGetLastError();
             return nullptr;
         }
         ptrs.push_back(p);
         return (T*)p;
     }
     ~Arena() {
-        for (void* p : ptrs) cudaFreeAsync(p, st);
+        for (void* p : ptrs) dev_free(p, st);
     }
 };
 
@@ -921,10 +981,75 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 if (rc) return rc;
             }
             side.rejoin();
+            // W ascending for matrices that split (see k_rank)
             tl.begin(MRRR_PHASE_FINISH);
-            k_sort_fix<X><<<grid_for(P, 32), 32, 0, st>>>(d_mats, P);
-            tl.end();
-            MRRR_CK(cudaGetLastError());
+            int fin_launches = 0;
+            {
+                std::vector<MatrixDesc> hm(P);
+                MRRR_CK(cudaMemcpyAsync(hm.data(), d_mats, sizeof(MatrixDesc) * P, cudaMemcpyDeviceToHost, st));
+                MRRR_CK(cudaStreamSynchronize(st));
+                std::vector<int> sp;
+                std::vector<long long> roff;
+                long long rtot = 0;
+                int maxk = 0;
+                for (int p = 0; p < P; ++p) {
+                    if (hm[p].nblocks > 1 && hm[p].kout > 1) {
+                        sp.push_back(p);
+                        roff.push_back(rtot);
+                        rtot += hm[p].kout;
+                        maxk = std::max(maxk, hm[p].kout);
+                    }
+                }
+                if (!sp.empty()) {
+                    const int ns = (int)sp.size();
+                    MRRR_ALLOC(d_sp, int, ns);
+                    MRRR_ALLOC(d_roff, long long, ns);
+                    MRRR_ALLOC(d_rank, int, rtot);
+                    MRRR_ALLOC(d_flag, int, ns);
+                    MRRR_CK(cudaMemcpyAsync(d_sp, sp.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+                    MRRR_CK(cudaMemcpyAsync(d_roff, roff.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, st));
+                    MRRR_CK(cudaMemsetAsync(d_flag, 0, sizeof(int) * ns, st));
+                    k_rank<X><<<dim3((maxk + kRankTile - 1) / kRankTile, ns), kRankTile, 0, st>>>(d_mats, d_sp, d_roff,
+                                                                                                 d_rank, d_flag);
+                    MRRR_CK(cudaGetLastError());
+                    ++fin_launches;
+                    std::vector<int> flag(ns);
+                    MRRR_CK(cudaMemcpyAsync(flag.data(), d_flag, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+                    MRRR_CK(cudaStreamSynchronize(st));
+                    // the matrices that must be permuted, with their offsets
+                    std::vector<int> fl;
+                    std::vector<long long> froff, ftoff;
+                    long long ttot = 0;
+                    int maxkf = 0;
+                    for (int q = 0; q < ns; ++q) {
+                        if (!flag[q]) continue;
+                        const MatrixDesc& M = hm[sp[q]];
+                        fl.push_back(sp[q]);
+                        froff.push_back(roff[q]);
+                        ftoff.push_back(ttot);
+                        ttot += (long long)M.n * M.kout;
+                        maxkf = std::max(maxkf, M.kout);
+                    }
+                    if (!fl.empty()) {
+                        const int nf = (int)fl.size();
+                        MRRR_ALLOC(d_fl, int, nf);
+                        MRRR_ALLOC(d_froff, long long, nf);
+                        MRRR_ALLOC(d_ftoff, long long, nf);
+                        MRRR_ALLOC(d_T, X, ttot);
+                        MRRR_ALLOC(d_Wt, X, rtot);
+                        MRRR_CK(cudaMemcpyAsync(d_fl, fl.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+                        MRRR_CK(cudaMemcpyAsync(d_froff, froff.data(), sizeof(long long) * nf, cudaMemcpyHostToDevice,
+                                                st));
+                        MRRR_CK(cudaMemcpyAsync(d_ftoff, ftoff.data(), sizeof(long long) * nf, cudaMemcpyHostToDevice,
+                                                st));
+                        k_gather<X><<<dim3(maxkf, nf), 128, 0, st>>>(d_mats, d_fl, d_froff, d_rank, d_ftoff, d_T, d_Wt);
+                        k_copy_back<X><<<dim3(maxkf, nf), 128, 0, st>>>(d_mats, d_fl, d_froff, d_ftoff, d_T, d_Wt);
+                        MRRR_CK(cudaGetLastError());
+                        fin_launches += 2;
+                    }
+                }
+            }
+            tl.end(fin_launches);
         }
     }
     MRRR_CK(cudaMemcpyAsync(&C, d_C, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));

@@ -104,3 +104,51 @@ def test_strerror_and_version():
     assert "argument" in m.strerror(m.MRRR_ERR_ARG)
     assert m.strerror(12345) == "unknown status"
     assert "sm_103a" in m.mrrr_version()
+
+
+def _struct_fields(name):
+    src = open(HEADER).read()
+    body = src.split("} %s;" % name)[0].rsplit("typedef struct {", 1)[1]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = re.match(r"((?:const\s+)?(?:long long|int|double|void\*|mrrr_mode))\s+(.*)", decl).groups()
+        for nm in names.split(","):
+            out.append((ctype, nm.strip()))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("mrrr_serve_config", "MrrrServeConfig"), ("mrrr_request", "MrrrRequest"),
+                                          ("mrrr_serve_info", "MrrrServeInfo"), ("mrrr_serve_stats", "MrrrServeStats")])
+def test_serve_structs_match_header(cname, pyname):
+    fields = _struct_fields(cname)
+    py = getattr(m, pyname)
+    assert [n for _, n in fields] == [f for f, _ in py._fields_]
+    sizes = {"int": 4, "mrrr_mode": 4, "long long": 8, "double": 8, "void*": 8, "const void*": 8}
+    for (ctype, nm), (fname, ftype) in zip(fields, py._fields_):
+        assert ctypes.sizeof(ftype) == sizes[ctype], nm
+
+
+def test_serve_arguments_rejected_without_device_work():
+    L = m.lib()
+    t = ctypes.c_longlong(0)
+    req = m.MrrrRequest()
+    assert L.mrrr_serve_submit(None, ctypes.byref(req), ctypes.byref(t)) == m.MRRR_ERR_ARG
+    assert L.mrrr_serve_poll(None, 1, 0, None) == m.MRRR_ERR_ARG
+    assert L.mrrr_serve_stats_get(None, None) == m.MRRR_ERR_ARG
+    assert L.mrrr_serve_close(None) == m.MRRR_ERR_ARG
+    assert L.mrrr_serve_open(None, None) == m.MRRR_ERR_ARG
+    bad = m.MrrrServeConfig(-1, 0, 0)
+    h = ctypes.c_void_p()
+    assert L.mrrr_serve_open(ctypes.byref(bad), ctypes.byref(h)) == m.MRRR_ERR_ARG
+
+
+def test_serve_open_without_device_fails_loudly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    h = ctypes.c_void_p()
+    assert m.lib().mrrr_serve_open(None, ctypes.byref(h)) == m.MRRR_ERR_CUDA

@@ -145,6 +145,17 @@ def test_split_matrix_with_tied_blocks(prec):
     assert st["nblocks"] == 6
 
 
+def test_split_many_identical_blocks_fp32():
+    # 120 glued W_21 copies with coupling 1e-8: below the fp32 split threshold
+    # (eps_x ||T||), so the matrix splits into 120 identical blocks whose
+    # eigenvalues tie 120-fold; the final values come out in a rounding-
+    # dependent order and are put in ascending order with their columns
+    d, e = inputs.glued_wilkinson(120, 21, 1e-8)
+    W, Z, st = _full_check(d, e, "s", "mixed", vectors=False)
+    assert st["nblocks"] == 120
+    assert np.all(np.diff(W) >= 0)
+
+
 @pytest.mark.parametrize("prec", ["s", "d"])
 def test_degenerate_inputs(prec):
     # diagonal matrix (every block of size 1), zero matrix, n = 1
