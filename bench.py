@@ -38,6 +38,21 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 FLOPS_PER_STEP = {"bisect": 4.0, "refine": 4.0, "rqi": 7.5, "shift": 5.0}
 PHASE_COUNTER = {"bisect": "qd_bisect", "refine": "qd_refine", "rqi": "qd_rqi", "shift": "qd_shift"}
 PHASE_KERNEL = {"bisect": "k_bisect", "refine": "k_bisect", "rqi": "k_rqi", "shift": "k_shift"}
+# DRAM bytes (read + write) per k_rqi launch on this workload, the mean over the
+# launches of one `ncu --set full` capture; valid only while the sources that
+# define the kernel hash to the value they had at the capture
+RQI_TRAFFIC = {"bytes_per_launch": 528.7e6, "sources_sha1": "c05fbbb8b5699091238a5e2dda8544c6ed3a6bf7",
+               "sources": ("mrrr_core.cuh", "mrrr_dd.cuh", "mrrr_fast.cuh", "mrrr_phases.cuh", "mrrr_solver.cuh",
+                           "mrrr_types.cuh", "solver_s.cu")}
+
+
+def _rqi_traffic():
+    import hashlib
+    h = hashlib.sha1()
+    for f in RQI_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_1304_1864_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return RQI_TRAFFIC["bytes_per_launch"] if h.hexdigest() == RQI_TRAFFIC["sources_sha1"] else None
 
 
 def _workload():
@@ -329,8 +344,12 @@ def run_ours(args):
     flops = acc[PHASE_COUNTER[dom]] * FLOPS_PER_STEP[dom]
     launches_dom = acc["n_" + dom]
     achieved = flops / (phase_ms[dom] / 1e3) / 1e9 if phase_ms[dom] > 0 else 0.0
+    traffic = _rqi_traffic() if PHASE_KERNEL[dom] == "k_rqi" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None, "kernel": PHASE_KERNEL[dom],
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                "traffic_note": ("bytes per launch, mean of the launches of one ncu capture of this kernel on this "
+                                 "workload" if traffic else "kernel changed since the last ncu capture"),
+                "kernel": PHASE_KERNEL[dom],
                 "phase": dom, "launches": launches_dom,
                 "ms_per_launch": phase_ms[dom] / max(launches_dom, 1),
                 "flops_per_launch": flops / max(launches_dom, 1),

@@ -101,7 +101,7 @@ typedef struct {
                           MIXED 1e-5 (s/d), 1e-10 (d/dd)] */
     double xi;         /* bound of the random relative perturbation of the root
                           representation, Algorithm 1 line 2 [PLAIN 8 eps_x; MIXED 4 eps_x] */
-    double krs;        /* RQI stopping constant k_rs, Eq. (3.5) [1] */
+    double krs;        /* RQI stopping constant k_rs, Eq. (2.2) and (3.8) [1] */
     int max_depth;     /* depth cap of the representation tree [16] */
     int max_rqi;       /* RQI steps before the bisection fallback [10] */
     uint64_t seed;     /* seed of the perturbation sequence [0] */

@@ -775,7 +775,7 @@ MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratc
 // each step solves at lambda, updates the bracket with the inertia of the
 // stationary part, and corrects lambda by gamma_r / ||z||^2.  It stops when
 // the residual |gamma_r| / ||z|| is below k_rs gap eps_x sqrt(n) (mixed,
-// Sec. 3.2) or k_rs gap n eps / gaptol (plain, Eq. 2.3), or when the
+// Sec. 3.2) or k_rs gap n eps / gaptol (plain, Eq. 2.2), or when the
 // correction stagnates below 4 eps_y |lambda|.  If the correction leaves the
 // bracket or the step budget runs out, lambda is bisected to relative
 // accuracy eps_x sqrt(n) gaptol (mixed) / n eps (plain) and one twisted solve

@@ -9,7 +9,7 @@ EPS = {"s": 2.0 ** -24, "d": 2.0 ** -53}
 # Tolerances (in units of n eps_x ||T||_1 for residuals and eigenvalues,
 # n eps_x for orthogonality).  Mixed precision: the targets the method is
 # meant to reach (eigenvalues within 2 n eps ||T||, residual and
-# orthogonality <= 1).  Plain (y = x): Eq. (2.3) stops the RQI at
+# orthogonality <= 1).  Plain (y = x): Eq. (2.2) stops the RQI at
 # k_rs gap n eps / gaptol and Theorem 1 bounds orthogonality by
 # O(n eps / gaptol); with gaptol = 1e-3 (x = d) or 3e-3 (x = s) that is
 # 1000 n eps for both.
