@@ -48,6 +48,11 @@ cudaMemPool_t pool_for_current_device() {
         }
         uint64_t keep = ~0ULL;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        // a block freed on one stream is not handed to another stream by
+        // making that stream wait for the first one: independent solves on
+        // different streams must not be chained through the allocator
+        int no = 0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
         g_pool[dev] = pool;
         g_pool_ok[dev] = true;
     }
@@ -67,6 +72,46 @@ void* dev_alloc(size_t bytes, cudaStream_t st) {
 
 void dev_free(void* p, cudaStream_t st) {
     if (p) cudaFreeAsync(p, st);
+}
+
+// Pinned host blocks for the solver's small readbacks and uploads, by
+// power-of-two size class (>= 4 KiB), kept for reuse.
+namespace {
+std::mutex g_host_mu;
+std::vector<std::pair<size_t, void*>> g_host_free;
+size_t host_class(size_t bytes) {
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    return c;
+}
+}  // namespace
+
+void* host_alloc(size_t bytes, size_t* got) {
+    const size_t c = host_class(bytes);
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        for (size_t i = 0; i < g_host_free.size(); ++i) {
+            if (g_host_free[i].first == c) {
+                void* p = g_host_free[i].second;
+                g_host_free.erase(g_host_free.begin() + (long)i);
+                *got = c;
+                return p;
+            }
+        }
+    }
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *got = c;
+    return p;
+}
+
+void host_free(void* p, size_t got) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    g_host_free.emplace_back(got, p);
 }
 
 }  // namespace mrrr

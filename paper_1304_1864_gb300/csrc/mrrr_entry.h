@@ -10,9 +10,15 @@ namespace mrrr {
 // Stream-ordered device memory of the library: one memory pool per device,
 // created on first use, that keeps freed blocks cached for the next solve
 // (release threshold: no limit) instead of returning them to the driver at
-// every synchronisation.  alloc returns nullptr on failure.
+// every synchronisation, and never reuses a block across streams by
+// inserting a wait between them.  alloc returns nullptr on failure.
 void* dev_alloc(size_t bytes, cudaStream_t st);
 void dev_free(void* p, cudaStream_t st);
+// Pinned host memory for small copies between host and device (a copy from
+// or to pageable memory goes through a synchronous staging path of the
+// driver).  *got receives the block's size, to pass back to host_free.
+void* host_alloc(size_t bytes, size_t* got);
+void host_free(void* p, size_t got);
 
 // binary32 input/output: working precision binary64 (mixed) or binary32 (plain)
 int solve_batch_s_mixed(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,

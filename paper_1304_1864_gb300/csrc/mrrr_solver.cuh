@@ -687,6 +687,46 @@ struct Arena {
     }
 };
 
+// Pinned host staging for one solve: every block handed out stays valid
+// until the solve returns, so an upload never has to wait for its copy.
+struct HostArena {
+    std::vector<std::pair<void*, size_t>> blocks;
+    bool failed = false;
+    template <class T> T* get(size_t count) {
+        size_t got = 0;
+        void* p = host_alloc(std::max<size_t>(count, 1) * sizeof(T), &got);
+        if (!p) {
+            failed = true;
+            return nullptr;
+        }
+        blocks.emplace_back(p, got);
+        return (T*)p;
+    }
+    ~HostArena() {
+        for (auto& b : blocks) host_free(b.first, b.second);
+    }
+};
+
+// Copies between host data and the device through pinned staging.
+template <class T>
+int to_device(HostArena& ha, T* dst, const T* src, size_t count, cudaStream_t st) {
+    T* h = ha.get<T>(count);
+    if (!h) return MRRR_ERR_NOMEM;
+    memcpy(h, src, sizeof(T) * count);
+    return cudaMemcpyAsync(dst, h, sizeof(T) * count, cudaMemcpyHostToDevice, st) == cudaSuccess ? 0 : MRRR_ERR_CUDA;
+}
+
+template <class T>
+int from_device(HostArena& ha, T* dst, const T* src, size_t count, cudaStream_t st) {
+    T* h = ha.get<T>(count);
+    if (!h) return MRRR_ERR_NOMEM;
+    if (cudaMemcpyAsync(h, src, sizeof(T) * count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return MRRR_ERR_CUDA;
+    memcpy(dst, h, sizeof(T) * count);
+    return 0;
+}
+
 #define MRRR_CK(call)                                  \
     do {                                               \
         cudaError_t err__ = (call);                    \
@@ -806,15 +846,15 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
     MRRR_ALLOC(d_C, DevCounters, 1);
     MRRR_ALLOC(d_total, int, 1);
     MRRR_CK(cudaMemsetAsync(d_C, 0, sizeof(DevCounters), st));
-    MRRR_CK(cudaMemcpyAsync(d_mats, mats, sizeof(MatrixDesc) * P, cudaMemcpyHostToDevice, st));
+    HostArena ha;
+    if (int rc0 = to_device(ha, d_mats, mats, (size_t)P, st)) return rc0;
 
     // a1: scale + split
     tl.begin(MRRR_PHASE_PREP);
     k_prep<X><<<P, 256, 0, st>>>(d_mats, d_blocks, wd, we, cfg);
     tl.end();
     MRRR_CK(cudaGetLastError());
-    MRRR_CK(cudaMemcpyAsync(mats, d_mats, sizeof(MatrixDesc) * P, cudaMemcpyDeviceToHost, st));
-    MRRR_CK(cudaStreamSynchronize(st));
+    if (int rc0 = from_device(ha, mats, d_mats, (size_t)P, st)) return rc0;
     std::vector<int> blist;
     for (int p = 0; p < P; ++p)
         for (int b = 0; b < mats[p].nblocks; ++b) blist.push_back(mats[p].row0 + b);
@@ -822,7 +862,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
     DevCounters C{};
     if (NB > 0) {
         MRRR_ALLOC(d_blist, int, NB);
-        MRRR_CK(cudaMemcpyAsync(d_blist, blist.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, st));
+        if (int rc0 = to_device(ha, d_blist, blist.data(), (size_t)NB, st)) return rc0;
         // a2: root representations
         tl.begin(MRRR_PHASE_ROOT);
         k_root<Y, Lo><<<NB, kRootThreads, 0, st>>>(d_blist, d_blocks, d_mats, wd, we, reps, reps_lo, cfg);
@@ -830,9 +870,8 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         tl.end(2);
         MRRR_CK(cudaGetLastError());
         int K = 0;
-        MRRR_CK(cudaMemcpyAsync(&K, d_total, sizeof(int), cudaMemcpyDeviceToHost, st));
-        MRRR_CK(cudaMemcpyAsync(mats, d_mats, sizeof(MatrixDesc) * P, cudaMemcpyDeviceToHost, st));
-        MRRR_CK(cudaStreamSynchronize(st));
+        if (int rc0 = from_device(ha, &K, d_total, 1, st)) return rc0;
+        if (int rc0 = from_device(ha, mats, d_mats, (size_t)P, st)) return rc0;
         if (K > 0) {
             MRRR_ALLOC(items, Item, K);
             MRRR_ALLOC(single_list, int, K);
@@ -951,8 +990,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                                                                  members, d_C);
                 tl.end();
                 MRRR_CK(cudaGetLastError());
-                MRRR_CK(cudaMemcpyAsync(&C, d_C, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-                MRRR_CK(cudaStreamSynchronize(st));
+                if (int rc0 = from_device(ha, &C, d_C, 1, st)) return rc0;
                 if (level == 0) {
                     s_root = C.nsingle;
                     if (C.ncluster > 0 && s_root > 0) {
@@ -986,8 +1024,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             int fin_launches = 0;
             {
                 std::vector<MatrixDesc> hm(P);
-                MRRR_CK(cudaMemcpyAsync(hm.data(), d_mats, sizeof(MatrixDesc) * P, cudaMemcpyDeviceToHost, st));
-                MRRR_CK(cudaStreamSynchronize(st));
+                if (int rc0 = from_device(ha, hm.data(), d_mats, (size_t)P, st)) return rc0;
                 std::vector<int> sp;
                 std::vector<long long> roff;
                 long long rtot = 0;
@@ -1006,16 +1043,15 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                     MRRR_ALLOC(d_roff, long long, ns);
                     MRRR_ALLOC(d_rank, int, rtot);
                     MRRR_ALLOC(d_flag, int, ns);
-                    MRRR_CK(cudaMemcpyAsync(d_sp, sp.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
-                    MRRR_CK(cudaMemcpyAsync(d_roff, roff.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, st));
+                    if (int rc0 = to_device(ha, d_sp, sp.data(), (size_t)ns, st)) return rc0;
+                    if (int rc0 = to_device(ha, d_roff, roff.data(), (size_t)ns, st)) return rc0;
                     MRRR_CK(cudaMemsetAsync(d_flag, 0, sizeof(int) * ns, st));
                     k_rank<X><<<dim3((maxk + kRankTile - 1) / kRankTile, ns), kRankTile, 0, st>>>(d_mats, d_sp, d_roff,
                                                                                                  d_rank, d_flag);
                     MRRR_CK(cudaGetLastError());
                     ++fin_launches;
                     std::vector<int> flag(ns);
-                    MRRR_CK(cudaMemcpyAsync(flag.data(), d_flag, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
-                    MRRR_CK(cudaStreamSynchronize(st));
+                    if (int rc0 = from_device(ha, flag.data(), d_flag, (size_t)ns, st)) return rc0;
                     // the matrices that must be permuted, with their offsets
                     std::vector<int> fl;
                     std::vector<long long> froff, ftoff;
@@ -1037,11 +1073,9 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                         MRRR_ALLOC(d_ftoff, long long, nf);
                         MRRR_ALLOC(d_T, X, ttot);
                         MRRR_ALLOC(d_Wt, X, rtot);
-                        MRRR_CK(cudaMemcpyAsync(d_fl, fl.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, st));
-                        MRRR_CK(cudaMemcpyAsync(d_froff, froff.data(), sizeof(long long) * nf, cudaMemcpyHostToDevice,
-                                                st));
-                        MRRR_CK(cudaMemcpyAsync(d_ftoff, ftoff.data(), sizeof(long long) * nf, cudaMemcpyHostToDevice,
-                                                st));
+                        if (int rc0 = to_device(ha, d_fl, fl.data(), (size_t)nf, st)) return rc0;
+                        if (int rc0 = to_device(ha, d_froff, froff.data(), (size_t)nf, st)) return rc0;
+                        if (int rc0 = to_device(ha, d_ftoff, ftoff.data(), (size_t)nf, st)) return rc0;
                         k_gather<X><<<dim3(maxkf, nf), 128, 0, st>>>(d_mats, d_fl, d_froff, d_rank, d_ftoff, d_T, d_Wt);
                         k_copy_back<X><<<dim3(maxkf, nf), 128, 0, st>>>(d_mats, d_fl, d_froff, d_ftoff, d_T, d_Wt);
                         MRRR_CK(cudaGetLastError());
@@ -1052,9 +1086,8 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             tl.end(fin_launches);
         }
     }
-    MRRR_CK(cudaMemcpyAsync(&C, d_C, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-    MRRR_CK(cudaMemcpyAsync(mats, d_mats, sizeof(MatrixDesc) * P, cudaMemcpyDeviceToHost, st));
-    MRRR_CK(cudaStreamSynchronize(st));
+    if (int rc0 = from_device(ha, &C, d_C, 1, st)) return rc0;
+    if (int rc0 = from_device(ha, mats, d_mats, (size_t)P, st)) return rc0;
     int rc = 0;
     for (int p = 0; p < P && rc == 0; ++p) {
         if (mats[p].status == ST_ERR_NONFINITE) rc = MRRR_ERR_NONFINITE;
