@@ -27,6 +27,9 @@ constexpr int kThreads = 128;
 constexpr int kLatThreads = 32;
 // threads of the one-CTA-per-block root kernel
 constexpr int kRootThreads = 256;
+// persistent RQI grid: resident warps per SM (16 one-warp CTAs of 128
+// registers per thread fill the register file of an SM)
+constexpr int kRqiWarpsPerSM = 16;
 inline int grid_for(long long n, int threads = kThreads) { return (int)((n + threads - 1) / threads); }
 
 // ------------------------------------------------------------------ kernels
@@ -529,70 +532,80 @@ __global__ void k_shift(const Cluster* clusters, int nc, Item* items, const Bloc
     shift_cluster<Y, Lo>(clusters[t], items, blocks, pool, pool_lo, cfg, C);
 }
 
-// One thread per eigenpair of the list: at most pass_iters RQI steps;
-// unfinished eigenpairs go to park_list.  Finished vectors are written by
-// the whole warp: a 32 x 32 tile (32 rows of the 32 lanes' vectors) goes
-// through shared memory so that each column segment is one contiguous
-// 128-byte (binary32) / 256-byte (binary64) store, instead of 32 scattered
-// words per instruction.
+// Persistent RQI over a list of eigenpairs: one-warp CTAs, each warp takes
+// the next 32 entries of the list from a global counter (`queue`) until the
+// list is exhausted, so warps that finish early keep taking work and the
+// scratch belongs to the warp (2 nmax working-precision words per lane), not
+// to the eigenpair -- a batch of any size runs in one launch.  One thread
+// per eigenpair: at most pass_iters RQI steps; unfinished eigenpairs go to
+// park_list.  Finished vectors are written by the whole warp: a 32 x 32
+// tile (32 rows of the 32 lanes' vectors) goes through shared memory so that
+// each column segment is one contiguous 128-byte (binary32) / 256-byte
+// (binary64) store, instead of 32 scattered words per instruction.
 template <class X, class Y>
-__global__ void k_rqi(Item* items, const int* list, int w0, int count, const int* dev_total, MatrixDesc* mats,
+__global__ void k_rqi(Item* items, const int* list, int count, const int* dev_total, int* queue, MatrixDesc* mats,
                       const BlockDesc* blocks, SolveCfg cfg, Y* scratch, int nmax, DevCounters* C, int pass_iters,
                       int final_pass, int* park_list, int* park_count) {
     constexpr bool kCoop = !std::is_same<Y, dd>::value;
-    __shared__ X tile[kLatThreads / 32][32][33];
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    // list[w0 .. w0+count) is this launch's share; a later pass is launched
-    // for an upper bound and reads the true length of its list on the device
-    const bool active = t < count && (dev_total == nullptr || w0 + t < *dev_total);
-    if (!kCoop && !active) return;
-    int it = active ? list[w0 + t] : 0;
+    __shared__ X tile[32][33];
+    const int lane = threadIdx.x & 31;
+    // this warp's scratch slot (one-warp CTAs), reused for every chunk it takes
+    Y* base = scratch + ((size_t)blockIdx.x * 32 + lane) * (size_t)(2 * nmax);
     Scratch<Y> Wk;
-    Y* base = scratch + (size_t)(active ? t : 0) * (size_t)(2 * nmax);
     Wk.a = base;
     Wk.b = base + nmax;
     Wk.stride = 1;
-    double scale = 0.0;
-    bool stored = false;
-    if (active) {
-        Item& I = items[it];
-        stored = rqi_item<X, Y>(I, mats, blocks, cfg, Wk, C, pass_iters, final_pass != 0, kCoop ? &scale : nullptr);
-        if (!stored) {
-            int slot = atomicAdd(park_count, 1);
-            park_list[slot] = it;
+    // a later pass is launched for an upper bound and reads the true length
+    // of its list on the device
+    const int total = dev_total ? min(count, *dev_total) : count;
+    for (;;) {
+        int b0 = 0;
+        if (lane == 0) b0 = atomicAdd(queue, 32);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (b0 >= total) break;
+        const int t = b0 + lane;
+        const bool active = t < total;
+        const int it = active ? list[t] : 0;
+        double scale = 0.0;
+        bool stored = false;
+        if (active) {
+            Item& I = items[it];
+            stored = rqi_item<X, Y>(I, mats, blocks, cfg, Wk, C, pass_iters, final_pass != 0,
+                                    kCoop ? &scale : nullptr);
+            if (!stored) {
+                int slot = atomicAdd(park_count, 1);
+                park_list[slot] = it;
+            }
         }
-    }
-    if constexpr (kCoop) {
-        // warp-cooperative store of the finished vectors
-        int nrow = 0, ldz = 0;
-        X* col = nullptr;
-        if (stored) {
-            const Item& I = items[it];
-            const MatrixDesc& M = mats[I.matrix];
-            nrow = I.n;
-            ldz = M.ldz;
-            col = (X*)M.Z + (size_t)I.outcol * (size_t)ldz + blocks[I.block].mrow;
-        }
-        (void)ldz;
-        int nmaxw = nrow;
-        for (int o = 16; o > 0; o >>= 1) nmaxw = max(nmaxw, __shfl_xor_sync(0xffffffffu, nmaxw, o));
-        for (int r0 = 0; r0 < nmaxw; r0 += 32) {
-            // lane l: rows r0..r0+31 of its own vector into tile row l
+        if constexpr (kCoop) {
+            // warp-cooperative store of the finished vectors
+            int nrow = 0;
+            X* col = nullptr;
+            if (stored) {
+                const Item& I = items[it];
+                const MatrixDesc& M = mats[I.matrix];
+                nrow = I.n;
+                col = (X*)M.Z + (size_t)I.outcol * (size_t)M.ldz + blocks[I.block].mrow;
+            }
+            int nmaxw = nrow;
+            for (int o = 16; o > 0; o >>= 1) nmaxw = max(nmaxw, __shfl_xor_sync(0xffffffffu, nmaxw, o));
+            for (int r0 = 0; r0 < nmaxw; r0 += 32) {
+                // lane l: rows r0..r0+31 of its own vector into tile row l
 #pragma unroll 4
-            for (int q = 0; q < 32; ++q) {
-                int r = r0 + q;
-                tile[wib][lane][q] = (r < nrow) ? (X)(to_d(Wk.a[r]) * scale) : X(0);
+                for (int q = 0; q < 32; ++q) {
+                    int r = r0 + q;
+                    tile[lane][q] = (r < nrow) ? (X)(to_d(Wk.a[r]) * scale) : X(0);
+                }
+                __syncwarp();
+                // column c of the tile: lanes write 32 consecutive rows
+                for (int c = 0; c < 32; ++c) {
+                    X* cc = (X*)__shfl_sync(0xffffffffu, (unsigned long long)col, c);
+                    int nc = __shfl_sync(0xffffffffu, nrow, c);
+                    int r = r0 + lane;
+                    if (cc && r < nc) cc[r] = tile[c][lane];
+                }
+                __syncwarp();
             }
-            __syncwarp();
-            // column c of the tile: lanes write 32 consecutive rows
-            for (int c = 0; c < 32; ++c) {
-                X* cc = (X*)__shfl_sync(0xffffffffu, (unsigned long long)col, c);
-                int nc = __shfl_sync(0xffffffffu, nrow, c);
-                int r = r0 + lane;
-                if (cc && r < nc) cc[r] = tile[wib][c][lane];
-            }
-            __syncwarp();
         }
     }
 }
@@ -932,21 +945,30 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             tl.end();
             MRRR_CK(cudaGetLastError());
             size_t per = 2 * (size_t)nmax * sizeof(Y);
+            int num_sms = 0, dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms < 1)
+                num_sms = 152;
             // RQI in passes: two steps per eigenpair in the first pass (most
             // converge), then the parked ones, densely packed, in further
             // passes; the last pass has the rest of the max_rqi budget
             auto run_rqi = [&](int s0, int s1, cudaStream_t rs) -> int {
                 if (s1 <= s0) return 0;
                 const int S = s1 - s0;
-                long long wave = (long long)(ScratchBudget<Y>::bytes() / 2 / per);
-                wave = std::max<long long>(32, wave / 32 * 32);
-                wave = std::min<long long>(wave, ((long long)S + 31) / 32 * 32);
-                Y* scratch = arena.alloc<Y>((size_t)wave * 2 * nmax);
-                int* park = arena.alloc<int>(2 * (size_t)S + 2);
+                // persistent grid: enough warps for the list, at most
+                // kRqiWarpsPerSM per SM, and within the scratch budget
+                const size_t per_warp = 32 * per;
+                long long G = ((long long)S + 31) / 32;
+                G = std::min<long long>(G, (long long)num_sms * kRqiWarpsPerSM);
+                G = std::min<long long>(G, std::max<long long>(1, (long long)(ScratchBudget<Y>::bytes() / per_warp)));
+                Y* scratch = arena.alloc<Y>((size_t)G * 32 * 2 * nmax);
+                int* park = arena.alloc<int>(2 * (size_t)S + 5);
                 if (!scratch || !park) return MRRR_ERR_NOMEM;
                 int* park_a = park;
                 int* park_b = park + S;
-                int* counts = park + 2 * (size_t)S;  // two device counters
+                int* counts = park + 2 * (size_t)S;  // two park counters, three queue counters
+                int* queues = counts + 2;
+                if (cudaMemsetAsync(counts, 0, 5 * sizeof(int), rs) != cudaSuccess) return MRRR_ERR_CUDA;
                 const int kPasses = 3;
                 const int* list = single_list + s0;
                 const int* total = nullptr;  // the first pass has all S items
@@ -956,17 +978,12 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                     bool final_pass = pass == kPasses - 1;
                     int* out = (pass % 2 == 0) ? park_a : park_b;
                     int* cnt = counts + (pass % 2);
-                    if (!final_pass && cudaMemsetAsync(cnt, 0, sizeof(int), rs) != cudaSuccess) return MRRR_ERR_CUDA;
                     int iters = pass == 0 ? 2 : (final_pass ? cfg.max_rqi : 3);
-                    for (long long w0 = 0; w0 < S; w0 += wave) {
-                        int c = (int)std::min<long long>(wave, S - w0);
-                        tl.begin(MRRR_PHASE_RQI, rs);
-                        k_rqi<X, Y><<<grid_for(c, kLatThreads), kLatThreads, 0, rs>>>(items, list, (int)w0, c, total, d_mats, d_blocks,
-                                                                      cfg, scratch, nmax, d_C, iters,
-                                                                      final_pass ? 1 : 0, out, cnt);
-                        tl.end(1, rs);
-                        if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
-                    }
+                    tl.begin(MRRR_PHASE_RQI, rs);
+                    k_rqi<X, Y><<<(int)G, 32, 0, rs>>>(items, list, S, total, queues + pass, d_mats, d_blocks, cfg,
+                                                        scratch, nmax, d_C, iters, final_pass ? 1 : 0, out, cnt);
+                    tl.end(1, rs);
+                    if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
                     list = out;
                     total = cnt;
                 }
