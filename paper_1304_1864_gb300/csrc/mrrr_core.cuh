@@ -186,6 +186,38 @@ MRRR_HD int negcount_lo(const Lo* __restrict__ D, const Lo* __restrict__ LLD, in
     return cnt;
 }
 
+// Twist index for the first RQI step from the rounded low-precision copy
+// [D | LLD] of the representation: gamma_k = s_k + p_k + tau from the
+// stationary (s) and progressive (p) transforms at tau, r = argmin |gamma_k|
+// (Sec. 2, the twisted factorization's choice of r), in the low precision.
+// Only the index comes from here; the step itself -- gamma_r, the inertia
+// and the vector -- runs in the working precision at that r, and any r at
+// which the wanted eigenvector has a large entry serves.  s_store holds n
+// values of scratch.  Returns -1 if the sweep met a vanished pivot or an
+// overflow (the caller then factors fully in the working precision).
+template <class Lo>
+MRRR_HD int twist_index_lo(const Lo* __restrict__ D, const Lo* __restrict__ LLD, int n, Lo tau,
+                           Lo* __restrict__ s_store) {
+    Lo s = -tau;
+    for (int i = 0; i < n - 1; ++i) {
+        s_store[i] = s;
+        s = fdiv_lo(s * LLD[i], D[i] + s) - tau;
+    }
+    Lo p = D[n - 1] - tau;
+    Lo gbest = s + p + tau;
+    int r = n - 1;
+    for (int i = n - 2; i >= 0; --i) {
+        p = fdiv_lo(D[i] * p, LLD[i] + p) - tau;
+        Lo g = s_store[i] + p + tau;
+        if (fabs(g) <= fabs(gbest)) {  // smallest index on ties
+            gbest = g;
+            r = i;
+        }
+    }
+    if (!isfinite(gbest) || !isfinite(p) || !isfinite(s)) return -1;
+    return r;
+}
+
 // ------------------------------------------------------------ root representation
 
 // L D L^T factorization of (T - mu I) in working precision for the rows

@@ -180,8 +180,10 @@ __device__ __forceinline__ double dstqds_fast(const double* __restrict__ parent,
 // N_r^T z = e_r from l+ (A, rows < r) and u (B, rows >= r); z overwrites A.
 // Every lane runs n-1 steps -- first r steps downward from r (z_i = -l+_i
 // z_{i+1}), then n-1-r steps upward (z_{i+1} = -u_i z_i) -- so lanes with
-// different r do not diverge; the coefficient of the next step is loaded
-// one step ahead.  Returns ||z||^2; *imax = index of the largest |z_i|
+// different r do not diverge.  The common step is written with selects
+// instead of branches (the row index, the restart at r, the arg-max); only
+// a zero entry takes the zero rule.  The coefficients are loaded a group of
+// kG steps ahead.  Returns ||z||^2; *imax = index of the largest |z_i|
 // (smallest index on ties).
 __device__ __forceinline__ double solve_twisted_fast(const double* __restrict__ LD, int n, int r,
                                                      double* __restrict__ A, const double* __restrict__ B,
@@ -192,53 +194,50 @@ __device__ __forceinline__ double solve_twisted_fast(const double* __restrict__ 
     int im = r;
     double zprev = 1.0;   // z at the previous position of the walk
     double zprev2 = 0.0;  // z two positions back (for the zero rule)
-    // coefficient of walk step k: l+_{r-1-k} downward, u_k upward; loaded a
-    // group of kG steps ahead
+    const int steps = n - 1;
+    // coefficient of walk step k: l+_{r-1-k} downward, u_k upward
     double cur[kG], nxt[kG];
 #pragma unroll
-    for (int k = 0; k < kG; ++k) cur[k] = k < n - 1 ? (k < r ? A[r - 1 - k] : B[k]) : 0.0;
-    for (int k0 = 0; k0 < n - 1; k0 += kG) {
+    for (int k = 0; k < kG; ++k) {
+        const double* pp = k < r ? A + (r - 1 - k) : B + k;
+        cur[k] = k < steps ? *pp : 0.0;
+    }
+    for (int k0 = 0; k0 < steps; k0 += kG) {
 #pragma unroll
         for (int q = 0; q < kG; ++q) {
-            int kk = k0 + kG + q;
-            nxt[q] = kk < n - 1 ? (kk < r ? A[r - 1 - kk] : B[kk]) : 0.0;
+            const int kk = k0 + kG + q;
+            const double* pp = kk < r ? A + (r - 1 - kk) : B + kk;
+            nxt[q] = kk < steps ? *pp : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < kG; ++q) {
-            int k = k0 + q;
-            if (k < n - 1) {
-                int i;
-                bool down = k < r;
-                if (down) {
-                    i = r - 1 - k;
-                } else {
-                    i = k + 1;
-                    if (k == r) {  // the upward walk restarts at z_r = 1
-                        zprev = 1.0;
-                        zprev2 = 0.0;
+            const int k = k0 + q;
+            if (k < steps) {
+                const bool down = k < r;
+                const int i = down ? r - 1 - k : k + 1;
+                const bool reset = k == r;  // the upward walk restarts at z_r = 1
+                zprev = reset ? 1.0 : zprev;
+                zprev2 = reset ? 0.0 : zprev2;
+                double z = -(cur[q] * zprev);
+                if (dabsbits(zprev) == 0) {
+                    if (dabsbits(zprev2) == 0) {
+                        // two zeros in a row: the vector has underflowed and
+                        // stays zero from here on (no divide)
+                        z = 0.0;
+                    } else if (down) {
+                        // row i+1 with z_{i+1} = 0: e_i z_i + e_{i+1} z_{i+2} = 0
+                        z = (i + 2 < n) ? -(__ldg(LD + i + 1) / __ldg(LD + i)) * zprev2 : 0.0;
+                    } else {
+                        // row i-1 with z_{i-1} = 0: e_{i-2} z_{i-2} + e_{i-1} z_i = 0
+                        z = (i >= 2) ? -(__ldg(LD + i - 2) / __ldg(LD + i - 1)) * zprev2 : 0.0;
                     }
-                }
-                double z;
-                if (dabsbits(zprev) != 0) {
-                    z = -(cur[q] * zprev);
-                } else if (dabsbits(zprev2) == 0) {
-                    // two zeros in a row: the vector has underflowed and stays
-                    // zero from here on (no divide for these rows)
-                    z = 0.0;
-                } else if (down) {
-                    // row i+1 with z_{i+1} = 0: e_i z_i + e_{i+1} z_{i+2} = 0
-                    z = (i + 2 < n) ? -(__ldg(LD + i + 1) / __ldg(LD + i)) * zprev2 : 0.0;
-                } else {
-                    // row i-1 with z_{i-1} = 0: e_{i-2} z_{i-2} + e_{i-1} z_i = 0
-                    z = (i >= 2) ? -(__ldg(LD + i - 2) / __ldg(LD + i - 1)) * zprev2 : 0.0;
                 }
                 A[i] = z;
                 nrm2 = fma(z, z, nrm2);
-                unsigned long long za = dabsbits(z);
-                if (za > zmax || (za == zmax && i < im)) {
-                    zmax = za;
-                    im = i;
-                }
+                const unsigned long long za = dabsbits(z);
+                const bool better = za > zmax || (za == zmax && i < im);
+                zmax = better ? za : zmax;
+                im = better ? i : im;
                 zprev2 = zprev;
                 zprev = z;
             }
@@ -343,32 +342,54 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
         }
         bad = bad || !dfinite(p);
     } else {
+        // fixed r: rows < r of the stationary transform (l+ -> A) and rows
+        // > r of the progressive one (u -> B, counting the signs of the
+        // pivots w_{i+1}), as one walk of n-1 steps per lane -- r stationary
+        // rows top-down, then n-1-r progressive rows bottom-up -- so lanes
+        // with different r do not diverge.  Both rows have the form
+        // q = 1 / (a + x), m = b q, with (a, b) = (d_i, ld_i) and the update
+        // x = x (m l_i) - lam for the stationary row, (a, b) = (lld_i, d_i)
+        // and x = x m - lam for the progressive one.
         r = r_fixed;
-        // rows < r of the stationary transform (l+ -> A, no s needed)
-        double s = stationary_fast(D, L, LD, r, lam, A, nullptr, &neg);
-        // rows > r of the progressive transform (u -> B), counting w_{i+1} < 0
-        double p = __ldg(D + n - 1) - lam;
-        int c = 0;
-        if (r < n - 1) {
-            double lldn = __ldg(LLD + n - 2), dn = __ldg(D + n - 2), lnx = __ldg(L + n - 2);
-            for (int i = n - 2; i >= r; --i) {
-                double lldi = lldn, di = dn, li = lnx;
-                if (i > r) {
-                    lldn = __ldg(LLD + i - 1);
-                    dn = __ldg(D + i - 1);
-                    lnx = __ldg(L + i - 1);
-                }
-                double om = lldi + p;
-                c += dsign(om);
-                double t = di * drcp<2>(om);
-                B[i] = li * t;
-                p = fma(p, t, -lam);
+        const double dlast = __ldg(D + n - 1) - lam;
+        double x = -lam, s_r = 0.0;
+        if (r == 0) {
+            s_r = x;
+            x = dlast;
+        }
+        bool st = 0 < r;
+        int i = st ? 0 : n - 2;
+        double a = __ldg((st ? D : LLD) + i), b = __ldg((st ? LD : D) + i), l = __ldg(L + i);
+        for (int k = 0; k < n - 1; ++k) {
+            const int ic = i;
+            const bool stc = st;
+            const double ac = a, bc = b, lc = l;
+            // operands of the next step, one step ahead
+            const int k1 = k + 1;
+            st = k1 < r;
+            i = st ? k1 : n - 2 - (k1 - r);
+            if (k1 < n - 1) {
+                a = __ldg((st ? D : LLD) + i);
+                b = __ldg((st ? LD : D) + i);
+                l = __ldg(L + i);
+            }
+            const double den = ac + x;
+            neg += dsign(den);
+            const double m = bc * drcp<2>(den);
+            const double ml = m * lc;
+            *((stc ? A : B) + ic) = stc ? m : ml;
+            x = fma(x, stc ? ml : m, -lam);
+            if (k1 == r) {
+                s_r = x;
+                x = dlast;
             }
         }
-        neg += c;
-        gbest = s + p + lam;
+        // the switch after row r-1 has run for every r >= 1 (for r = n-1 at
+        // the last step, leaving p_{n-1} = d_{n-1} - lam)
+        const double p = x;
+        gbest = s_r + p + lam;
         neg += dsign(gbest);
-        bad = !dfinite(s) || !dfinite(p) || !dfinite(gbest);
+        bad = !dfinite(s_r) || !dfinite(p) || !dfinite(gbest);
     }
     if (bad) return twisted_guarded(rep, n, lam, pivmin, A, B, gamma, imax);
     res.nrm2 = solve_twisted_fast(LD, n, r, A, B, imax);

@@ -316,6 +316,11 @@ MRRR_HD bool separated(const Item& A, const Item& B, double gaptol) {
 MRRR_HD bool same_group(const Item& A, const Item& B) { return A.rep == B.rep && A.block == B.block; }
 
 
+// Precision of the rounded copy of a rep: binary32 for binary32/binary64
+// reps, binary64 for double-double reps.
+template <class Y> struct LowType { typedef float T; };
+template <> struct LowType<dd> { typedef double T; };
+
 template <class T> MRRR_HD T bmax(const T& a, const T& b) { return a < b ? b : a; }
 template <class T> MRRR_HD T bmin(const T& a, const T& b) { return b < a ? b : a; }
 MRRR_HD double babs(double x) { return fabs(x); }
@@ -811,13 +816,23 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         if constexpr (std::is_same<Y, dd>::value) lam = dd(I.lam_hi, I.lam_lo);
         else lam = from_d<Y>(I.lam_hi);
     }
+    if (I.rqi_done == 0 && pass_iters == 2 && !final_pass) {
+        // first pass: predict whether two steps suffice.  Every step solves
+        // with the right-hand side e_r, so the shift error contracts like
+        // e -> c e^2 / gap (c ~ 1/2 measured) and the residual after the
+        // next solve is ~10 e; an eigenpair whose e0 (half the bracket) does
+        // not pass 5 e0^2 / gap <= tol gets its third step in this pass
+        // rather than in a later, nearly empty launch
+        const double e0 = 0.5 * (I.hi - I.lo);
+        if (5.0 * e0 * e0 > tol * gap) pass_iters = 3;
+    }
     Y gamma = from_d<Y>(0.0);
     TwistResult<Y> tr;
     Y lam_out = lam;
     bool conv = false;
     int iters = 0;
     int imax_t = -1;
-    unsigned long long steps = 0;
+    unsigned long long steps = 0, steps_low = 0;
     if (n == 1) {
         Wk.A(0) = from_d<Y>(1.0);
         tr.r = 0;
@@ -826,8 +841,16 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         conv = true;
     } else {
         // after the first step the twist index is the largest entry of the
-        // previous iterate (one pass of the transforms instead of two)
+        // previous iterate (one pass of the transforms instead of two); the
+        // first step takes it from a low-precision sweep over the rounded
+        // copy of the rep, so it too needs one working-precision pass
         int r_hint = I.rhint;
+        if (I.rqi_done == 0 && r_hint < 0 && I.rep_lo != nullptr) {
+            typedef typename LowType<Y>::T Lo;
+            const Lo* Dl = (const Lo*)I.rep_lo;
+            r_hint = twist_index_lo<Lo>(Dl, Dl + n, n, (Lo)to_d(lam), (Lo*)Wk.a);
+            steps_low = 2ULL * n;
+        }
         const int done0 = I.rqi_done;
         for (int it = 0; it < pass_iters && done0 + it < cfg.max_rqi; ++it) {
             tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t, r_hint);
@@ -871,6 +894,7 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
             I.rhint = r_hint;
             MRRR_ATOMIC_ADD(&C->rqi_iters, iters);
             MRRR_ATOMIC_ADD(&C->qd_rqi, steps);
+            if (steps_low) MRRR_ATOMIC_ADD(&C->qd_steps_low, steps_low);
             return false;
         }
         if (!conv) {
@@ -915,6 +939,7 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     }
     MRRR_ATOMIC_ADD(&C->rqi_iters, iters);
     MRRR_ATOMIC_ADD(&C->qd_rqi, steps);
+    if (steps_low) MRRR_ATOMIC_ADD(&C->qd_steps_low, steps_low);
     // eigenvalue of T: (lambda + sigma) / scale
     dd lt = dd(to_d(lam_out)) + dd(I.sig_hi, I.sig_lo);
     if constexpr (std::is_same<Y, dd>::value) lt = lam_out + dd(I.sig_hi, I.sig_lo);
