@@ -337,49 +337,86 @@ template <class Y> struct TwistResult {
 // One twisted-factorization solve at shift lam (Sec. 2, RQI steps (i)-(iii)):
 // stationary transform top-down (l+ -> A, s -> B), progressive transform
 // bottom-up (gamma_k, u -> B), r = argmin |gamma_k|, then N_r^T z = e_r with z
-// written into A.  Returns gamma_r through *gamma.
+// written into A.  Returns gamma_r through *gamma.  With r_fixed >= 0 the
+// twist index is given and only rows < r of the stationary and rows > r of
+// the progressive transform are formed, as one walk of n-1 rows (r
+// stationary rows top-down, then the progressive rows bottom-up; both have
+// the form m = b / (a + x)); the inertia of the twisted factorization,
+// diag(d+_0..d+_{r-1}, gamma_r, w_{r+1}..w_{n-1}), is the Sturm count at lam
+// either way (Sylvester).  If imax != null it receives the index of the
+// largest |z_i| (smallest index on ties), the twist index for a next step.
 template <class Y>
-MRRR_HD TwistResult<Y> twisted_solve(const Y* rep, int n, Y lam, Y pivmin, const Scratch<Y>& W, Y* gamma) {
+MRRR_HD TwistResult<Y> twisted_solve(const Y* rep, int n, Y lam, Y pivmin, const Scratch<Y>& W, Y* gamma,
+                                     int r_fixed = -1, int* imax = nullptr) {
     typedef typename Acc<Y>::T A_t;
     RepPtr<Y> P(rep, n);
     TwistResult<Y> res;
-    // stationary, top-down
-    Y s = -lam;
     int neg = 0;
-    for (int i = 0; i < n - 1; ++i) {
-        Y dp = P.D[i] + s;
-        if (ysmall(dp, pivmin)) dp = -pivmin;
-        neg += yneg(dp) ? 1 : 0;
-        Y lp = qdiv<Y>(P.LD[i], dp);
-        W.A(i) = lp;
-        W.B(i) = s;
-        s = lp * P.L[i] * s - lam;
-    }
-    {
-        Y dp = P.D[n - 1] + s;
-        if (ysmall(dp, pivmin)) dp = -pivmin;
-        neg += yneg(dp) ? 1 : 0;
-    }
-    // progressive, bottom-up
-    Y p = P.D[n - 1] - lam;
-    Y gbest = s + p + lam;
-    int r = n - 1;
-    for (int i = n - 2; i >= 0; --i) {
-        Y om = P.LLD[i] + p;
-        if (ysmall(om, pivmin)) om = -pivmin;
-        Y t = qdiv<Y>(P.D[i], om);
-        Y um = P.L[i] * t;
-        p = p * t - lam;
-        Y g = W.B(i) + p + lam;
-        W.B(i) = um;
-        if (!(yabs(g) > yabs(gbest))) {  // <= (NaN never wins)
-            gbest = g;
-            r = i;
+    int r;
+    Y gbest;
+    if (r_fixed < 0) {
+        // stationary, top-down
+        Y s = -lam;
+        for (int i = 0; i < n - 1; ++i) {
+            Y dp = P.D[i] + s;
+            if (ysmall(dp, pivmin)) dp = -pivmin;
+            neg += yneg(dp) ? 1 : 0;
+            Y lp = qdiv<Y>(P.LD[i], dp);
+            W.A(i) = lp;
+            W.B(i) = s;
+            s = lp * P.L[i] * s - lam;
         }
+        {
+            Y dp = P.D[n - 1] + s;
+            if (ysmall(dp, pivmin)) dp = -pivmin;
+            neg += yneg(dp) ? 1 : 0;
+        }
+        // progressive, bottom-up
+        Y p = P.D[n - 1] - lam;
+        gbest = s + p + lam;
+        r = n - 1;
+        for (int i = n - 2; i >= 0; --i) {
+            Y om = P.LLD[i] + p;
+            if (ysmall(om, pivmin)) om = -pivmin;
+            Y t = qdiv<Y>(P.D[i], om);
+            Y um = P.L[i] * t;
+            p = p * t - lam;
+            Y g = W.B(i) + p + lam;
+            W.B(i) = um;
+            if (!(yabs(g) > yabs(gbest))) {  // <= (NaN never wins)
+                gbest = g;
+                r = i;
+            }
+        }
+    } else {
+        r = r_fixed;
+        const Y dlast = P.D[n - 1] - lam;
+        Y x = -lam, s_r = -lam;
+        if (r == 0) x = dlast;
+        for (int k = 0; k < n - 1; ++k) {
+            const bool st = k < r;
+            const int i = st ? k : n - 2 - (k - r);
+            Y den = (st ? P.D[i] : P.LLD[i]) + x;
+            if (ysmall(den, pivmin)) den = -pivmin;
+            neg += yneg(den) ? 1 : 0;
+            const Y m = qdiv<Y>(st ? P.LD[i] : P.D[i], den);
+            const Y ml = m * P.L[i];
+            if (st) W.A(i) = m;
+            else W.B(i) = ml;
+            x = x * (st ? ml : m) - lam;
+            if (k + 1 == r) {  // the stationary rows are done: s_r, then the progressive start
+                s_r = x;
+                x = dlast;
+            }
+        }
+        gbest = s_r + x + lam;
+        neg += yneg(gbest) ? 1 : 0;
     }
     // N_r^T z = e_r
     A_t nrm2 = A_t(1.0);
     W.A(r) = from_d<Y>(1.0);
+    double zbig = 1.0;
+    int im = r;
     for (int i = r - 1; i >= 0; --i) {
         Y zn = W.A(i + 1);
         Y z;
@@ -392,6 +429,11 @@ MRRR_HD TwistResult<Y> twisted_solve(const Y* rep, int n, Y lam, Y pivmin, const
         W.A(i) = z;
         A_t za = A_t(z);
         nrm2 += za * za;
+        double az = fabs(to_d(z));
+        if (az >= zbig) {  // walking down: >= keeps the smallest index on ties
+            zbig = az;
+            im = i;
+        }
     }
     for (int i = r; i < n - 1; ++i) {
         Y zc = W.A(i);
@@ -405,7 +447,13 @@ MRRR_HD TwistResult<Y> twisted_solve(const Y* rep, int n, Y lam, Y pivmin, const
         W.A(i + 1) = z;
         A_t za = A_t(z);
         nrm2 += za * za;
+        double az = fabs(to_d(z));
+        if (az > zbig) {
+            zbig = az;
+            im = i + 1;
+        }
     }
+    if (imax) *imax = im;
     res.r = r;
     res.neg = neg;
     res.nrm2 = nrm2;

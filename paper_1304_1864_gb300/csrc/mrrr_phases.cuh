@@ -770,7 +770,9 @@ MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratc
         if (Wk.stride == 1) return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax, r_hint);
     }
 #endif
-    (void)r_hint;
+    // double-double (and the emulating host build): the generic solve, at
+    // the given twist index when there is one
+    if constexpr (std::is_same<Y, dd>::value) return twisted_solve<Y>(rep, n, lam, pm, Wk, gamma, r_hint, imax);
     *imax = -1;
     return twisted_solve<Y>(rep, n, lam, pm, Wk, gamma);
 }
@@ -845,7 +847,9 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         // first step takes it from a low-precision sweep over the rounded
         // copy of the rep, so it too needs one working-precision pass
         int r_hint = I.rhint;
-        if (I.rqi_done == 0 && r_hint < 0 && I.rep_lo != nullptr) {
+        // (where a fixed-r step exists: binary64 and double-double)
+        if ((std::is_same<Y, double>::value || std::is_same<Y, dd>::value) && I.rqi_done == 0 && r_hint < 0 &&
+            I.rep_lo != nullptr) {
             typedef typename LowType<Y>::T Lo;
             const Lo* Dl = (const Lo*)I.rep_lo;
             r_hint = twist_index_lo<Lo>(Dl, Dl + n, n, (Lo)to_d(lam), (Lo*)Wk.a);
