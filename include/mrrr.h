@@ -90,6 +90,7 @@ typedef struct {
     long long qd_low;     /* qd steps of the pre-bisection in a precision below the working one */
     int verify_fail;      /* pre-bisection brackets widened by the working-precision check */
     int reps_relaxed;     /* child reps accepted only under the relaxed growth bound of Eq. (3.6) */
+    int rqi_warps_per_sm; /* resident warps per SM of the persistent RQI grid (largest RQI list) */
     int timed;            /* 1 if phase_ms / phase_launches were measured (MRRR_FLAG_TIMING) */
     int phase_launches[MRRR_NPHASES]; /* kernel launches per phase */
     double phase_ms[MRRR_NPHASES];    /* device time per phase (CUDA events on the solve's stream) */
@@ -114,6 +115,7 @@ typedef struct {
 #define MRRR_FLAG_TIMING 4            /* time every phase with CUDA events (fills stats->phase_ms) */
 #define MRRR_FLAG_STRICT_GROWTH 8     /* MIXED: accept child reps only under the y = x growth bound,
                                          not the relaxed bound of Sec. 3.2, Eq. (3.6) */
+#define MRRR_FLAG_NO_TUNE 16          /* use the default RQI grid instead of the autotuned one */
 
 /*
  * Single-precision input/output (x = binary32).  MRRR_MIXED computes in

@@ -16,7 +16,7 @@ MRRR_ALL, MRRR_INDEX, MRRR_VALUE = 0, 1, 2
 MRRR_PLAIN, MRRR_MIXED = 0, 1
 MRRR_OK, MRRR_ERR_ARG, MRRR_ERR_NONFINITE, MRRR_ERR_NOCONV = 0, -1, -2, -3
 MRRR_ERR_NOMEM, MRRR_ERR_CUDA, MRRR_ERR_TIMEOUT, MRRR_ERR_NOREP = -4, -5, -6, -7
-MRRR_FLAG_NO_LOWPREC_BISECT, MRRR_FLAG_TIMING, MRRR_FLAG_STRICT_GROWTH = 1, 4, 8
+MRRR_FLAG_NO_LOWPREC_BISECT, MRRR_FLAG_TIMING, MRRR_FLAG_STRICT_GROWTH, MRRR_FLAG_NO_TUNE = 1, 4, 8, 16
 NPHASES = 8
 PHASES = ("prep", "root", "bisect", "classify", "shift", "refine", "rqi", "finish")
 
@@ -27,7 +27,7 @@ class MrrrStats(ctypes.Structure):
                 ("fallbacks", ctypes.c_int), ("noconv", ctypes.c_int),
                 ("qd_bisect", ctypes.c_longlong), ("qd_refine", ctypes.c_longlong), ("qd_rqi", ctypes.c_longlong),
                 ("qd_shift", ctypes.c_longlong), ("qd_low", ctypes.c_longlong), ("verify_fail", ctypes.c_int),
-                ("reps_relaxed", ctypes.c_int),
+                ("reps_relaxed", ctypes.c_int), ("rqi_warps_per_sm", ctypes.c_int),
                 ("timed", ctypes.c_int), ("phase_launches", ctypes.c_int * NPHASES),
                 ("phase_ms", ctypes.c_double * NPHASES)]
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <unordered_map>
 
 #include <cmath>
 #include <cstring>
@@ -112,6 +113,46 @@ void host_free(void* p, size_t got) {
     if (!p) return;
     std::lock_guard<std::mutex> lk(g_host_mu);
     g_host_free.emplace_back(got, p);
+}
+
+namespace {
+struct TuneState {
+    int next = 0;                            // next candidate to try
+    float ms[kRqiTuneCandidates] = {0, 0, 0};
+    int reported = 0;                        // candidates with a time
+    int chosen = -1;
+};
+std::mutex g_tune_mu;
+std::unordered_map<unsigned, TuneState> g_tune;
+}  // namespace
+
+int rqi_tune_pick(unsigned key, int* trial) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneState& t = g_tune[key];
+    if (t.chosen >= 0) {
+        *trial = -1;
+        return kRqiTuneWarps[t.chosen];
+    }
+    if (t.next < kRqiTuneCandidates) {
+        *trial = t.next++;
+        return kRqiTuneWarps[*trial];
+    }
+    // every candidate handed out, some still running: use the first meanwhile
+    *trial = -1;
+    return kRqiTuneWarps[0];
+}
+
+void rqi_tune_report(unsigned key, int trial, float ms) {
+    if (trial < 0 || trial >= kRqiTuneCandidates) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneState& t = g_tune[key];
+    t.ms[trial] = ms;
+    if (++t.reported == kRqiTuneCandidates) {
+        int best = 0;
+        for (int c = 1; c < kRqiTuneCandidates; ++c)
+            if (t.ms[c] < t.ms[best]) best = c;
+        t.chosen = best;
+    }
 }
 
 }  // namespace mrrr

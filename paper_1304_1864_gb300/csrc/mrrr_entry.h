@@ -20,6 +20,19 @@ void dev_free(void* p, cudaStream_t st);
 void* host_alloc(size_t bytes, size_t* got);
 void host_free(void* p, size_t got);
 
+// Online autotuner of the persistent RQI grid (resident one-warp CTAs per
+// SM).  Workloads are grouped into classes by `key` (working precision, and
+// the magnitudes of the list length and of the largest n).  The first runs
+// of a class try the candidates kRqiTuneWarps in turn and report their time;
+// afterwards the fastest is used.  The choice only changes scheduling: each
+// eigenpair's arithmetic, and so every result, is the same for every grid.
+constexpr int kRqiTuneCandidates = 3;
+constexpr int kRqiTuneWarps[kRqiTuneCandidates] = {16, 8, 4};
+// returns the warps per SM to use; *trial = the candidate to time in this
+// run, or -1 once the class is decided
+int rqi_tune_pick(unsigned key, int* trial);
+void rqi_tune_report(unsigned key, int trial, float ms);
+
 // binary32 input/output: working precision binary64 (mixed) or binary32 (plain)
 int solve_batch_s_mixed(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
                         mrrr_stats* stats);

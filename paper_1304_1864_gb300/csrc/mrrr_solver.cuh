@@ -27,9 +27,6 @@ constexpr int kThreads = 128;
 constexpr int kLatThreads = 32;
 // threads of the one-CTA-per-block root kernel
 constexpr int kRootThreads = 256;
-// persistent RQI grid: resident warps per SM (16 one-warp CTAs of 128
-// registers per thread fill the register file of an SM)
-constexpr int kRqiWarpsPerSM = 16;
 inline int grid_for(long long n, int threads = kThreads) { return (int)((n + threads - 1) / threads); }
 
 // ------------------------------------------------------------------ kernels
@@ -829,6 +826,13 @@ template <class Y> struct ScratchBudget {
 // one).  mats[p] carries the input/output device pointers, n, ldz and range;
 // the remaining fields are filled in.  Returns 0 or a negative status; the
 // per-matrix status and count are left in mats[p].status / mats[p].kout.
+// An autotuner trial: the RQI passes of one run, bracketed by two events.
+struct TuneRun {
+    unsigned key;
+    int trial;
+    cudaEvent_t a, b;
+};
+
 template <class X, class Y>
 int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
                 mrrr_stats* stats) {
@@ -873,6 +877,8 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         for (int b = 0; b < mats[p].nblocks; ++b) blist.push_back(mats[p].row0 + b);
     const int NB = (int)blist.size();
     DevCounters C{};
+    int rqi_wps = 0, rqi_wps_list = 0;
+    std::vector<TuneRun> tune_runs;  // timed autotuner trials, reported after the final synchronisation
     if (NB > 0) {
         MRRR_ALLOC(d_blist, int, NB);
         if (int rc0 = to_device(ha, d_blist, blist.data(), (size_t)NB, st)) return rc0;
@@ -955,11 +961,26 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             auto run_rqi = [&](int s0, int s1, cudaStream_t rs) -> int {
                 if (s1 <= s0) return 0;
                 const int S = s1 - s0;
-                // persistent grid: enough warps for the list, at most
-                // kRqiWarpsPerSM per SM, and within the scratch budget
+                // persistent grid: enough warps for the list, at most the
+                // tuned number of warps per SM, and within the scratch budget
                 const size_t per_warp = 32 * per;
                 long long G = ((long long)S + 31) / 32;
-                G = std::min<long long>(G, (long long)num_sms * kRqiWarpsPerSM);
+                int trial = -1;
+                unsigned key = 0;
+                int wps = kRqiTuneWarps[0];
+                if (G > (long long)num_sms * kRqiTuneWarps[kRqiTuneCandidates - 1] &&
+                    !(cfg.flags & MRRR_FLAG_NO_TUNE)) {
+                    // only lists that can fill more than the smallest grid
+                    // have anything to tune
+                    auto lg = [](long long v) { unsigned b = 0; while (v > 1) { v >>= 1; ++b; } return b; };
+                    key = (unsigned)sizeof(Y) << 16 | lg(S) << 8 | lg(nmax);
+                    wps = rqi_tune_pick(key, &trial);
+                }
+                if (S > rqi_wps_list) {  // report the grid of the largest list
+                    rqi_wps = wps;
+                    rqi_wps_list = S;
+                }
+                G = std::min<long long>(G, (long long)num_sms * wps);
                 G = std::min<long long>(G, std::max<long long>(1, (long long)(ScratchBudget<Y>::bytes() / per_warp)));
                 Y* scratch = arena.alloc<Y>((size_t)G * 32 * 2 * nmax);
                 int* park = arena.alloc<int>(2 * (size_t)S + 5);
@@ -972,6 +993,9 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 const int kPasses = 3;
                 const int* list = single_list + s0;
                 const int* total = nullptr;  // the first pass has all S items
+                cudaEvent_t ta = nullptr, tb = nullptr;
+                if (trial >= 0 && cudaEventCreate(&ta) == cudaSuccess && cudaEventCreate(&tb) == cudaSuccess)
+                    cudaEventRecord(ta, rs);
                 // no host synchronisation between passes: the stream (possibly
                 // the side stream) keeps running while the host goes on
                 for (int pass = 0; pass < kPasses; ++pass) {
@@ -986,6 +1010,10 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                     if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
                     list = out;
                     total = cnt;
+                }
+                if (ta && tb) {
+                    cudaEventRecord(tb, rs);
+                    tune_runs.push_back({key, trial, ta, tb});
                 }
                 return 0;
             };
@@ -1105,6 +1133,12 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
     }
     if (int rc0 = from_device(ha, &C, d_C, 1, st)) return rc0;
     if (int rc0 = from_device(ha, mats, d_mats, (size_t)P, st)) return rc0;
+    for (TuneRun& t : tune_runs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) rqi_tune_report(t.key, t.trial, ms);
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
     int rc = 0;
     for (int p = 0; p < P && rc == 0; ++p) {
         if (mats[p].status == ST_ERR_NONFINITE) rc = MRRR_ERR_NONFINITE;
@@ -1126,6 +1160,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         stats->qd_low = (long long)C.qd_steps_low;
         stats->verify_fail = C.verify_fail;
         stats->reps_relaxed = C.reps_relaxed;
+        stats->rqi_warps_per_sm = rqi_wps;
         tl.collect(stats);
     }
     if (arena.failed) return MRRR_ERR_NOMEM;
