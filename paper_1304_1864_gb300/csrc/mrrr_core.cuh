@@ -119,6 +119,23 @@ MRRR_HD float fdiv_lo(float a, float b) {
 }
 MRRR_HD double fdiv_lo(double a, double b) { return qdiv<double>(a, b); }
 
+// Software prefetch into L2 for the row loops.  A lane streams through its
+// own representation (a child rep of a cluster, or the scratch of its
+// eigenpair) one row per step, and each row is one dependent chain of
+// FP64 latency long; loading only the next row leaves DRAM latency exposed
+// whenever the rep is not cache resident.  The loops therefore ask for the
+// line kPrefetch rows ahead (a line holds 16 binary64 / 32 binary32 values;
+// the caller keeps the row inside the array).  No register is tied up and
+// the host build ignores it.
+constexpr int kPrefetch = 64;
+MRRR_HD void pf_l2(const void* p) {
+#if defined(__CUDA_ARCH__)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#else
+    (void)p;
+#endif
+}
+
 // ------------------------------------------------------------ random perturbation
 
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) as a counter-based generator:
@@ -175,6 +192,9 @@ MRRR_HD int negcount_lo(const Lo* __restrict__ D, const Lo* __restrict__ LLD, in
     Lo s = -tau;
     int cnt = 0;
     for (int i = 0; i < n - 1; ++i) {
+        const int ip = min(i + kPrefetch, n - 1);
+        pf_l2(D + ip);
+        pf_l2(LLD + ip);
         Lo dp = D[i] + s;
         if (!(fabs(dp) >= pivmin)) dp = -pivmin;  // also catches NaN
         cnt += dp < Lo(0) ? 1 : 0;
@@ -200,6 +220,9 @@ MRRR_HD int twist_index_lo(const Lo* __restrict__ D, const Lo* __restrict__ LLD,
                            Lo* __restrict__ s_store) {
     Lo s = -tau;
     for (int i = 0; i < n - 1; ++i) {
+        const int ip = min(i + kPrefetch, n - 1);
+        pf_l2(D + ip);
+        pf_l2(LLD + ip);
         s_store[i] = s;
         s = fdiv_lo(s * LLD[i], D[i] + s) - tau;
     }
@@ -207,6 +230,10 @@ MRRR_HD int twist_index_lo(const Lo* __restrict__ D, const Lo* __restrict__ LLD,
     Lo gbest = s + p + tau;
     int r = n - 1;
     for (int i = n - 2; i >= 0; --i) {
+        const int ip = max(i - kPrefetch, 0);
+        pf_l2(D + ip);
+        pf_l2(LLD + ip);
+        pf_l2(s_store + ip);
         p = fdiv_lo(D[i] * p, LLD[i] + p) - tau;
         Lo g = s_store[i] + p + tau;
         if (fabs(g) <= fabs(gbest)) {  // smallest index on ties

@@ -21,6 +21,7 @@
 #pragma once
 
 #include <cfloat>
+#include <algorithm>
 #include <cmath>
 
 #if defined(__CUDACC__)
@@ -39,6 +40,8 @@ using std::fmin;
 using std::frexp;
 using std::isfinite;
 using std::ldexp;
+using std::max;
+using std::min;
 using std::nextafter;
 using std::sqrt;
 #endif

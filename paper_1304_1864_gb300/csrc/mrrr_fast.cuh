@@ -64,6 +64,9 @@ __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const
     int i = 0;
     // four rows per iteration with their loads issued together
     for (; i + 4 <= n - 1; i += 4) {
+        const int ip = min(i + kPrefetch, n - 1);
+        pf_l2(D + ip);
+        pf_l2(LLD + ip);
         double d0 = __ldg(D + i), d1 = __ldg(D + i + 1), d2 = __ldg(D + i + 2), d3 = __ldg(D + i + 3);
         double l0 = __ldg(LLD + i), l1 = __ldg(LLD + i + 1), l2 = __ldg(LLD + i + 2), l3 = __ldg(LLD + i + 3);
         double dp = d0 + s;
@@ -100,6 +103,10 @@ __device__ __forceinline__ double stationary_fast(const double* __restrict__ D, 
     int c = 0;
     double dn = __ldg(D), ldn = __ldg(LD), lnx = __ldg(L);
     for (int i = 0; i < m; ++i) {
+        const int ip = min(i + kPrefetch, m);
+        pf_l2(D + ip);
+        pf_l2(LD + ip);
+        pf_l2(L + ip);
         double di = dn, ldi = ldn, li = lnx;
         dn = __ldg(D + i + 1);
         ldn = __ldg(LD + i + 1);
@@ -203,6 +210,10 @@ __device__ __forceinline__ double solve_twisted_fast(const double* __restrict__ 
         cur[k] = k < steps ? *pp : 0.0;
     }
     for (int k0 = 0; k0 < steps; k0 += kG) {
+        {
+            const int kp = min(k0 + kPrefetch, steps - 1);
+            pf_l2(kp < r ? A + (r - 1 - kp) : B + kp);
+        }
 #pragma unroll
         for (int q = 0; q < kG; ++q) {
             const int kk = k0 + kG + q;
@@ -226,10 +237,12 @@ __device__ __forceinline__ double solve_twisted_fast(const double* __restrict__ 
                         z = 0.0;
                     } else if (down) {
                         // row i+1 with z_{i+1} = 0: e_i z_i + e_{i+1} z_{i+2} = 0
-                        z = (i + 2 < n) ? -(__ldg(LD + i + 1) / __ldg(LD + i)) * zprev2 : 0.0;
+                        // (the quotient by the transforms' reciprocal, not an
+                        // IEEE divide: localized vectors take this rule often)
+                        z = (i + 2 < n) ? -(__ldg(LD + i + 1) * drcp<2>(__ldg(LD + i))) * zprev2 : 0.0;
                     } else {
                         // row i-1 with z_{i-1} = 0: e_{i-2} z_{i-2} + e_{i-1} z_i = 0
-                        z = (i >= 2) ? -(__ldg(LD + i - 2) / __ldg(LD + i - 1)) * zprev2 : 0.0;
+                        z = (i >= 2) ? -(__ldg(LD + i - 2) * drcp<2>(__ldg(LD + i - 1))) * zprev2 : 0.0;
                     }
                 }
                 A[i] = z;
@@ -314,6 +327,13 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
 #pragma unroll
         for (int k = 0; k < kG; ++k) cur[k] = (n - 2 - k >= 0) ? B[n - 2 - k] : 0.0;
         for (int i0 = n - 2; i0 >= 0; i0 -= kG) {
+            {
+                const int ip = max(i0 - kPrefetch, 0);
+                pf_l2(LLD + ip);
+                pf_l2(D + ip);
+                pf_l2(L + ip);
+                pf_l2(B + ip);
+            }
 #pragma unroll
             for (int k = 0; k < kG; ++k) {
                 int ii = i0 - kG - k;
@@ -364,7 +384,16 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
             const int ic = i;
             const bool stc = st;
             const double ac = a, bc = b, lc = l;
-            // operands of the next step, one step ahead
+            // operands of the next step, one step ahead; their lines
+            // kPrefetch steps ahead into L2
+            {
+                const int kp = min(k + kPrefetch, n - 2);
+                const bool sp = kp < r;
+                const int ipf = sp ? kp : n - 2 - (kp - r);
+                pf_l2((sp ? D : LLD) + ipf);
+                pf_l2((sp ? LD : D) + ipf);
+                pf_l2(L + ipf);
+            }
             const int k1 = k + 1;
             st = k1 < r;
             i = st ? k1 : n - 2 - (k1 - r);

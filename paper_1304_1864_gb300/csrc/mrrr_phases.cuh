@@ -770,9 +770,11 @@ MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratc
         if (Wk.stride == 1) return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax, r_hint);
     }
 #endif
-    // double-double (and the emulating host build): the generic solve, at
-    // the given twist index when there is one
-    if constexpr (std::is_same<Y, dd>::value) return twisted_solve<Y>(rep, n, lam, pm, Wk, gamma, r_hint, imax);
+    // double-double, and the host build of binary64 (which follows the
+    // device's steps): the generic solve, at the given twist index when
+    // there is one
+    if constexpr (std::is_same<Y, dd>::value || std::is_same<Y, double>::value)
+        return twisted_solve<Y>(rep, n, lam, pm, Wk, gamma, r_hint, imax);
     *imax = -1;
     return twisted_solve<Y>(rep, n, lam, pm, Wk, gamma);
 }
