@@ -41,7 +41,7 @@ PHASE_KERNEL = {"bisect": "k_bisect", "refine": "k_bisect", "rqi": "k_rqi", "shi
 # DRAM bytes (read + write) per k_rqi launch on this workload, the mean over the
 # launches of one `ncu --set full` capture; valid only while the sources that
 # define the kernel hash to the value they had at the capture
-RQI_TRAFFIC = {"bytes_per_launch": 528.7e6, "sources_sha1": "c05fbbb8b5699091238a5e2dda8544c6ed3a6bf7",
+RQI_TRAFFIC = {"bytes_per_launch": 404.7e6, "sources_sha1": "7fe9c0f570013d00d8ffbf5a310589ee91b87443",
                "sources": ("mrrr_core.cuh", "mrrr_dd.cuh", "mrrr_fast.cuh", "mrrr_phases.cuh", "mrrr_solver.cuh",
                            "mrrr_types.cuh", "solver_s.cu")}
 
