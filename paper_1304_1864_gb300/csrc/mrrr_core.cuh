@@ -444,12 +444,15 @@ MRRR_HD TwistResult<Y> twisted_solve(const Y* rep, int n, Y lam, Y pivmin, const
     W.A(r) = from_d<Y>(1.0);
     double zbig = 1.0;
     int im = r;
+    // (a zero next to a zero or a value below 2^-900 is the underflowed tail
+    // of a localized vector: it stays zero, without reviving subnormals)
+    const double ztiny = 0x1p-900;
     for (int i = r - 1; i >= 0; --i) {
         Y zn = W.A(i + 1);
         Y z;
         if (to_d(zn) == 0.0 && i + 2 < n) {
             // row i+1 of the tridiagonal with z_{i+1} = 0: e_i z_i + e_{i+1} z_{i+2} = 0
-            z = -(P.LD[i + 1] / P.LD[i]) * W.A(i + 2);
+            z = fabs(to_d(W.A(i + 2))) < ztiny ? from_d<Y>(0.0) : -(P.LD[i + 1] / P.LD[i]) * W.A(i + 2);
         } else {
             z = -(W.A(i) * zn);
         }
@@ -467,7 +470,7 @@ MRRR_HD TwistResult<Y> twisted_solve(const Y* rep, int n, Y lam, Y pivmin, const
         Y z;
         if (to_d(zc) == 0.0 && i >= 1) {
             // row i with z_i = 0: e_{i-1} z_{i-1} + e_i z_{i+1} = 0
-            z = -(P.LD[i - 1] / P.LD[i]) * W.A(i - 1);
+            z = fabs(to_d(W.A(i - 1))) < ztiny ? from_d<Y>(0.0) : -(P.LD[i - 1] / P.LD[i]) * W.A(i - 1);
         } else {
             z = -(W.B(i) * zc);
         }

@@ -31,6 +31,9 @@ __device__ __forceinline__ bool dfinite(double x) { return ((unsigned)__double2h
 
 // rows per software-prefetch group for the per-eigenpair scratch arrays
 constexpr int kG = 8;
+// bit pattern of 2^-900: entries of z (z_r = 1) below it are the underflowed
+// tail of the vector
+constexpr unsigned long long kZTinyBits = (unsigned long long)(1023 - 900) << 52;
 
 // reciprocal estimate refined by `steps` Newton-Raphson iterations
 template <int steps>
@@ -231,9 +234,11 @@ __device__ __forceinline__ double solve_twisted_fast(const double* __restrict__ 
                 zprev2 = reset ? 0.0 : zprev2;
                 double z = -(cur[q] * zprev);
                 if (dabsbits(zprev) == 0) {
-                    if (dabsbits(zprev2) == 0) {
-                        // two zeros in a row: the vector has underflowed and
-                        // stays zero from here on (no divide)
+                    if (dabsbits(zprev2) < kZTinyBits) {
+                        // a zero next to a zero or a value below 2^-900 (z_r =
+                        // 1): the underflowed tail of a localized vector,
+                        // which stays zero from here on (without this the
+                        // rule below would revive subnormals every other row)
                         z = 0.0;
                     } else if (down) {
                         // row i+1 with z_{i+1} = 0: e_i z_i + e_{i+1} z_{i+2} = 0
