@@ -815,6 +815,18 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     if (!(gap < INFINITY)) gap = fmax(B.spdiam, 1e-300);
     const double tol = cfg.mixed ? cfg.krs * gap * cfg.eps_x * sq : cfg.krs * gap * n * cfg.eps_y / cfg.gaptol;
     Y lo = from_d<Y>(I.lo), hi = from_d<Y>(I.hi);
+    if (std::is_same<Y, double>::value && I.rqi_done == 0) {
+        // the bracket was verified by the tuned binary64 count, whose
+        // reciprocal has one Newton step: it is exact for the rep perturbed
+        // element-wise by ~2^-44, so its eigenvalues can sit ~n 2^-44 |lambda|
+        // from the ones the full-precision steps below converge to.  Widen the
+        // safeguard by that much so a correct Rayleigh correction near an end
+        // is not rejected as leaving the bracket (the inertia of the first
+        // step narrows it again).
+        const double pad = 16.0 * n * 0x1p-44 * fmax(fabs(I.lo), fabs(I.hi)) + 4.0 * B.pivmin;
+        lo = from_d<Y>(I.lo - pad);
+        hi = from_d<Y>(I.hi + pad);
+    }
     Y lam = (lo + hi) * from_d<Y>(0.5);
     if (I.rqi_done > 0) {  // continue from the saved shift
         if constexpr (std::is_same<Y, dd>::value) lam = dd(I.lam_hi, I.lam_lo);
@@ -823,12 +835,12 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     if (I.rqi_done == 0 && pass_iters == 2 && !final_pass) {
         // first pass: predict whether two steps suffice.  Every step solves
         // with the right-hand side e_r, so the shift error contracts like
-        // e -> c e^2 / gap (c ~ 1/2 measured) and the residual after the
-        // next solve is ~10 e; an eigenpair whose e0 (half the bracket) does
-        // not pass 5 e0^2 / gap <= tol gets its third step in this pass
-        // rather than in a later, nearly empty launch
+        // e -> c e^2 / gap (c ~ 1/2 to 2/3 measured) and the residual after
+        // the next solve is ~10-20 e; an eigenpair whose e0 (half the
+        // bracket) does not pass 20 e0^2 / gap <= tol gets its third step in
+        // this pass rather than in a later, nearly empty launch
         const double e0 = 0.5 * (I.hi - I.lo);
-        if (5.0 * e0 * e0 > tol * gap) pass_iters = 3;
+        if (20.0 * e0 * e0 > tol * gap) pass_iters = 3;
     }
     Y gamma = from_d<Y>(0.0);
     TwistResult<Y> tr;
@@ -859,10 +871,18 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         }
         const int done0 = I.rqi_done;
         for (int it = 0; it < pass_iters && done0 + it < cfg.max_rqi; ++it) {
+            const bool r_from_sweep = it == 0 && done0 == 0 && r_hint >= 0;
             tr = twist_step<Y>(rep, n, lam, pm, Wk, &gamma, &imax_t, r_hint);
             steps += (r_hint < 0 ? 2ULL : 1ULL) * n;
             r_hint = imax_t;
             ++iters;
+            // a first step whose low-precision twist index missed the large
+            // entries of the vector (z_r = 1 but some |z_i| > 4) gives a poor
+            // Rayleigh correction: allow one step more in this pass rather than
+            // parking the eigenpair for a nearly empty later launch
+            if (r_from_sweep && !final_pass && imax_t >= 0 && pass_iters < 3 &&
+                fabs(to_d(Wk.A(imax_t))) > 4.0)
+                pass_iters = 3;
             if (tr.neg >= I.j) hi = bmin(hi, lam);
             else lo = bmax(lo, lam);
             double nrm2 = to_d(tr.nrm2);
@@ -874,14 +894,29 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
                 break;
             }
             Y nl = lam + corr;
-            if (lo < nl && nl < hi) {
+            // inside the bracket, or outside by no more than rounding: an end
+            // can sit within rounding of the eigenvalue (a pre-bisection point
+            // or an earlier iterate), and a correct step then lands a hair
+            // beyond it; a neighbouring eigenvalue is a whole gap away
+            const Y slack = from_d<Y>(16.0 * n * cfg.eps_y * fabs(to_d(lam)));
+            const Y width = hi - lo;
+            if (lo - slack < nl && nl < hi + slack) {
                 lam = nl;
+            } else if ((nl >= hi && nl - hi <= width * from_d<Y>(0.25)) ||
+                       (nl <= lo && lo - nl <= width * from_d<Y>(0.25))) {
+                // a short overshoot past an end that lies close to the
+                // eigenvalue: step to just inside that end (the vector, and
+                // so the twist index, stays good)
+                lam = nl >= hi ? hi - width * from_d<Y>(0x1p-10) : lo + width * from_d<Y>(0x1p-10);
             } else {
                 // the correction left the bracket (it points at another
                 // eigenvalue): take a bisection step instead, with the bracket
                 // just narrowed by the inertia at lam, and refactor fully
                 lam = (lo + hi) * from_d<Y>(0.5);
                 r_hint = -1;
+                // from the bisected shift the iteration needs about two more
+                // steps: take them in this pass
+                if (!final_pass && pass_iters < it + 3) pass_iters = it + 3;
             }
         }
         if (!conv && !final_pass && done0 + iters < cfg.max_rqi) {
