@@ -420,24 +420,25 @@ __global__ void k_verify(Item* items, const int* list, int count, const BlockDes
     if (!endpoint_holds(I, side, c) && atomicOr(&vflags[it], 1 << side) == 0) fix_list[atomicAdd(&C->nvfix, 1)] = it;
 }
 
-// kMS lanes per listed item move its failing ends.  For a failing lower end
-// x (count(x) >= j) the lanes test, in one sweep, the points x - w 4^k for
-// k = 1..kMS (the next sweep continues with k = kMS+1..2 kMS); the point
-// nearest to x whose count is < j is the new lower end, and the point tested
-// just before it -- whose count is still >= j, so it bounds lambda_j from
-// above -- the new upper end when that end did not fail too.  Symmetrically
-// for a failing upper end.  w is the first doubling step of the sequential
-// check (endpoint_step), so one sweep covers eight doublings.  After two
-// sweeps the end falls back to the sequential widening, which ends at the
+// kFixLanes lanes per listed item move its failing ends.  For a failing
+// lower end x (count(x) >= j) the lanes test, in one sweep, the points
+// x - w 4^k for k = 1..kFixLanes; the point nearest to x whose count is < j
+// is the new lower end, and the point tested just before it -- whose count
+// is still >= j, so it bounds lambda_j from above -- the new upper end when
+// that end did not fail too.  Symmetrically for a failing upper end.  w is
+// the first doubling step of the sequential check (endpoint_step), so the
+// sweep covers sixteen doublings with the latency of one count.  Beyond
+// that the end falls back to the sequential widening, which ends at the
 // bound of the whole spectrum.
-constexpr int kFixSweeps = 2;
+constexpr int kFixLanes = 8;
+constexpr int kFixSweeps = 1;
 template <class Y>
 __global__ void k_verify_fix(Item* items, const int* fix_list, int bound, const BlockDesc* blocks, DevCounters* C,
                              unsigned long long* step_counter, int* vflags) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int g = t / kMS, q = t % kMS;
-    if (g >= bound || g >= C->nvfix) return;  // whole groups leave together (kMS divides 32)
-    unsigned mask = ((1u << kMS) - 1u) << ((threadIdx.x & 31) & ~(kMS - 1));
+    int g = t / kFixLanes, q = t % kFixLanes;
+    if (g >= bound || g >= C->nvfix) return;  // whole groups leave together (kFixLanes divides 32)
+    unsigned mask = ((1u << kFixLanes) - 1u) << ((threadIdx.x & 31) & ~(kFixLanes - 1));
     const int it = fix_list[g];
     Item& I = items[it];
     const BlockDesc& B = blocks[I.block];
@@ -456,15 +457,15 @@ __global__ void k_verify_fix(Item* items, const int* fix_list, int bound, const 
         bool found = false;
         double p = x0;
         for (int sw = 0; sw < kFixSweeps && !found; ++sw) {
-            double f = ldexp(1.0, 2 * (sw * kMS + q + 1));  // 4^(k)
+            double f = ldexp(1.0, 2 * (sw * kFixLanes + q + 1));  // 4^(k)
             double xq = side ? x0 + w0[side] * f : x0 - w0[side] * f;
             int c = count_at<Y, true>(rep, rep + 3 * n, n, from_d<Y>(xq), pm);
             steps += (unsigned long long)n;
             bool ok = endpoint_holds(I, side, c);
 #pragma unroll
-            for (int k = 0; k < kMS; ++k) {
-                bool okk = __shfl_sync(mask, (int)ok, k, kMS) != 0;
-                double xk = __shfl_sync(mask, xq, k, kMS);
+            for (int k = 0; k < kFixLanes; ++k) {
+                bool okk = __shfl_sync(mask, (int)ok, k, kFixLanes) != 0;
+                double xk = __shfl_sync(mask, xq, k, kFixLanes);
                 if (found) continue;
                 if (okk) {
                     found = true;
@@ -480,7 +481,7 @@ __global__ void k_verify_fix(Item* items, const int* fix_list, int bound, const 
             Item J = I;
             if (side) J.hi = last_fail;
             else J.lo = last_fail;
-            p = widen_endpoint<Y>(J, B, side, w0[side] * ldexp(1.0, 2 * kFixSweeps * kMS), &steps, &fails);
+            p = widen_endpoint<Y>(J, B, side, w0[side] * ldexp(1.0, 2 * kFixSweeps * kFixLanes), &steps, &fails);
         }
         x[side] = p;
         // the last failing point bounds lambda_j on the other side
@@ -929,7 +930,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                     MRRR_CK(cudaMemsetAsync(&d_C->nvfix, 0, sizeof(int), st));
                     k_verify<Y><<<grid_for(2LL * count, kLatThreads), kLatThreads, 0, st>>>(
                         items, list, count, d_blocks, d_C, ctr, vflags, vfix_list);
-                    k_verify_fix<Y><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(
+                    k_verify_fix<Y><<<grid_for((long long)count * kFixLanes, kLatThreads), kLatThreads, 0, st>>>(
                         items, vfix_list, count, d_blocks, d_C, ctr, vflags);
                     MRRR_CK(cudaMemsetAsync(&d_C->nrefine, 0, sizeof(int), st));
                     k_certify<<<grid_for(count), kThreads, 0, st>>>(items, K, list, count, cfg.gaptol, refine_list,
