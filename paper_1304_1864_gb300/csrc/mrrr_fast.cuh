@@ -8,8 +8,10 @@
 //    so every FP64 instruction on a recurrence is latency.  Sign tests, the
 //    |gamma| comparison, zero tests and the arg-max are done on the IEEE bit
 //    patterns with integer instructions instead of FP64 compares.
-//  * The divide is a reciprocal estimate with Newton-Raphson refinement fused
-//    into the next operation (see qdiv).
+//  * The count carries the stationary transform in projective form (a
+//    numerator and a denominator) and needs no divide; in the twisted
+//    factorization the divide is a reciprocal estimate with Newton-Raphson
+//    refinement fused into the next operation (see qdiv).
 //  * Loads of the next row are issued one row ahead so memory latency
 //    overlaps the FP64 chain.
 #pragma once
@@ -48,51 +50,97 @@ __device__ __forceinline__ double drcp(double b) {
     return r;
 }
 
-// Sturm count (number of eigenvalues of L D L^T below tau) for bisection and
-// bracket checks.  The reciprocal gets one Newton step (relative error
-// ~2^-46): the count is exact for the rep perturbed element-wise by a few
-// units of 2^-46, far inside what classification needs (relative accuracy
-// 1e-2 gaptol >= 1e-12).  The loop runs unguarded; if a pivot vanished the
-// recurrence produces a non-finite value and the guarded count is used.
-// Guarded fallbacks, kept out of line so that they do not weigh on the
+// Guarded fallback, kept out of line so that it does not weigh on the
 // register allocation and scheduling of the unguarded hot loops.
 static __device__ __noinline__ int negcount_guarded(const double* D, const double* LLD, int n, double tau, double pivmin) {
     return negcount<double>(D, LLD, n, tau, pivmin);
 }
 
+// 1 if x is zero, subnormal, infinite or NaN (from the high word)
+__device__ __forceinline__ unsigned dnotnormal(double x) {
+    return (((unsigned)__double2hiint(x) & 0x7ff00000u) - 0x00100000u) >= 0x7fe00000u ? 1u : 0u;
+}
+
+// Power-of-two scaling of the projective recurrences: k with |x| 2^k in
+// [1, 2) for a normal x, clamped so that 2^k is normal (x is not normal only
+// on a path whose result is discarded), and 2^k for k in [-1022, 1023].
+__device__ __forceinline__ int dscale_exp(double x) {
+    const int e = (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
+    return max(1023 - e, -1022);
+}
+__device__ __forceinline__ double dpow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
+
+// A projective pair is rescaled when |X| leaves [2^-256, 2^256): a row
+// changes |X| by the pivot d+_i, so X stays normal unless a single pivot is
+// below ~2^-760.  A zero or subnormal X (a vanished pivot) is left as it is:
+// the projective recurrences need no special case for it.
+__device__ __forceinline__ bool dneeds_rescale(double x) {
+    const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+    return e != 0u && e - (1023u - 256u) >= 512u;
+}
+// Sturm count (number of eigenvalues of L D L^T below tau) for bisection and
+// bracket checks, without a divide.  The stationary transform maps s_i to
+// s_{i+1} = lld_i s_i / (d_i + s_i) - tau, a linear fractional map; writing
+// s_i = N_i / P_{i-1} (P_{-1} = 1, N_0 = -tau) turns it into the linear
+// recurrence
+//     P_i     = d_i P_{i-1} + N_i          (so d+_i = d_i + s_i = P_i / P_{i-1})
+//     N_{i+1} = lld_i N_i - tau P_i
+// and d+_i < 0 exactly when P_i and P_{i-1} have opposite signs.  With fused
+// multiply-adds d+_i is rounded once (as in the divide form) and s_{i+1}
+// twice (three times in the divide form), so the count is exact for the rep
+// perturbed element-wise by a few ulps -- the mixed relative stability of the
+// stationary qd transform (Sec. 2).  A row costs three FP64 instructions, two
+// of them on the dependency chain, against five and a reciprocal estimate for
+// the divide form.  Only the ratio N/P and the sign of P matter, so every
+// sixteen rows both are scaled by the power of two that brings P into [1, 2)
+// (after preprocessing a row changes |P| by a pivot of modest size).  A
+// vanished pivot needs no special case: P_i = +-0 counts d+_i as a pivot of
+// that sign and the recurrence continues from N_{i+1} = lld_i N_i (the limit
+// of the divide form); only an overflow, which leaves P or N non-finite,
+// sends the count to the guarded divide form.
 __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const double* __restrict__ LLD, int n,
                                              double tau, double pivmin) {
-    double s = -tau;
+    const double mtau = -tau;
+    double P = 1.0, N = mtau;
+    unsigned hp = 0u;  // high word of P_{i-1}
     int cnt = 0;
     int i = 0;
-    // four rows per iteration with their loads issued together
-    for (; i + 4 <= n - 1; i += 4) {
+    for (; i + 8 <= n - 1; i += 8) {
         const int ip = min(i + kPrefetch, n - 1);
         pf_l2(D + ip);
         pf_l2(LLD + ip);
-        double d0 = __ldg(D + i), d1 = __ldg(D + i + 1), d2 = __ldg(D + i + 2), d3 = __ldg(D + i + 3);
-        double l0 = __ldg(LLD + i), l1 = __ldg(LLD + i + 1), l2 = __ldg(LLD + i + 2), l3 = __ldg(LLD + i + 3);
-        double dp = d0 + s;
-        cnt += dsign(dp);
-        s = fma(s * l0, drcp<1>(dp), -tau);
-        dp = d1 + s;
-        cnt += dsign(dp);
-        s = fma(s * l1, drcp<1>(dp), -tau);
-        dp = d2 + s;
-        cnt += dsign(dp);
-        s = fma(s * l2, drcp<1>(dp), -tau);
-        dp = d3 + s;
-        cnt += dsign(dp);
-        s = fma(s * l3, drcp<1>(dp), -tau);
+        double d[8], l[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            d[k] = __ldg(D + i + k);
+            l[k] = __ldg(LLD + i + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const double a = l[k] * N;
+            P = fma(d[k], P, N);
+            const unsigned h = (unsigned)__double2hiint(P);
+            cnt += (int)((h ^ hp) >> 31);
+            hp = h;
+            N = fma(mtau, P, a);
+        }
+        if (i & 8) {  // every sixteen rows (the same rows in every lane)
+            const double f = dpow2(dscale_exp(P));
+            P *= f;
+            N *= f;
+        }
     }
     for (; i < n - 1; ++i) {
-        double dp = __ldg(D + i) + s;
-        cnt += dsign(dp);
-        s = fma(s * __ldg(LLD + i), drcp<1>(dp), -tau);
+        const double a = __ldg(LLD + i) * N;
+        P = fma(__ldg(D + i), P, N);
+        const unsigned h = (unsigned)__double2hiint(P);
+        cnt += (int)((h ^ hp) >> 31);
+        hp = h;
+        N = fma(mtau, P, a);
     }
-    double dp = __ldg(D + n - 1) + s;
-    cnt += dsign(dp);
-    if (!dfinite(s) || !dfinite(dp)) return negcount_guarded(D, LLD, n, tau, pivmin);
+    P = fma(__ldg(D + n - 1), P, N);
+    cnt += (int)((((unsigned)__double2hiint(P)) ^ hp) >> 31);
+    if (!dfinite(P) || !dfinite(N)) return negcount_guarded(D, LLD, n, tau, pivmin);
     return cnt;
 }
 
@@ -288,6 +336,179 @@ static __device__ __noinline__ TwistResult<double> twisted_guarded(const double*
     return res;
 }
 
+// steps of the twisted walk and solve whose operands are loaded ahead
+constexpr int kGp = 4;
+
+// Twisted factorization at a given twist index r in projective form, and
+// the solve N_r^T z = e_r (Sec. 2, RQI steps (i)-(iii)), without a divide
+// per row.
+//
+// The stationary rows i < r carry s_i = N_i / P_{i-1} (P_{-1} = 1,
+// N_0 = -lam):  P_i = d_i P_{i-1} + N_i (so d+_i = P_i / P_{i-1}) and
+// N_{i+1} = lld_i N_i - lam P_i, as in negcount_fast.  The progressive rows
+// i = n-2 .. r carry p_{i+1} = Q_{i+1} / R_{i+2} (R_n = 1,
+// Q_{n-1} = d_{n-1} - lam):  R_{i+1} = lld_i R_{i+2} + Q_{i+1} (so the pivot
+// of the progressive factorization is R_{i+1} / R_{i+2}) and
+// Q_i = d_i Q_{i+1} - lam R_{i+1}.  Both are one walk of n-1 steps per lane
+// -- r stationary rows top-down, then the progressive rows bottom-up -- of
+// the same form X' = a X + Y, Y' = b Y - lam X' with (a, b) = (d_i, lld_i)
+// or (lld_i, d_i), so that lanes with different r do not diverge.  A pivot
+// is negative where X changes sign; gamma_r = s_r + p_r + lam takes the
+// only two divides.
+//
+// With l+_i = ld_i P_{i-1} / P_i and u_i = ld_i R_{i+2} / R_{i+1} the solve
+// telescopes: z_i = w_i P_{i-1} for i < r with w_r = 1 / P_{r-1},
+// w_i = -ld_i w_{i+1}, and z_i = v_i R_{i+1} for i > r with
+// v_r = 1 / R_{r+1}, v_{i+1} = -ld_i v_i.  The walk stores the multiplier of
+// z_i (P_{i-1} or R_{i+1}) in A[i]; the solve overwrites it with z_i.  A
+// vanished pivot needs no special rule here (z_{i+1} = 0 and z_i follow
+// from the neighbouring multipliers), and the underflowed tail of a
+// localized vector stays zero.
+//
+// Where X leaves [2^-256, 2^256), X and Y are scaled by the power of two 2^k
+// that brings X into [1, 2) -- the ratios and the signs do not change --
+// right after X was stored, so that both the decision and k follow from the
+// stored value itself; the solve, reaching that entry, multiplies its
+// running factor by 2^k.  An overflow, or a vanished pivot at the twist
+// (P_{r-1} or R_{r+1} zero), sends the step to the guarded generic solve.
+__device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* __restrict__ rep, int n, double lam,
+                                                                 double pivmin, double* __restrict__ A,
+                                                                 double* __restrict__ B, double* gamma, int* imax,
+                                                                 int r) {
+    const double* __restrict__ D = rep;
+    const double* __restrict__ LD = rep + 2 * n;
+    const double* __restrict__ LLD = rep + 3 * n;
+    const double mlam = -lam;
+    const int steps = n - 1;
+    int neg = 0;
+    // walk step k: row k of the stationary chain for k < r, else row
+    // n-2-(k-r) of the progressive one
+    auto wrow = [&](int k) { return k < r ? k : n - 2 - (k - r); };
+    // top chain state (P_{i-1}, N_i); for r = 0 the chain is empty
+    double X = 1.0, Y = r > 0 ? mlam : __ldg(D + n - 1) - lam;
+    double Xtop = 1.0, Ytop = mlam;
+    unsigned hx = (unsigned)__double2hiint(X);
+    double ca[kGp], cb[kGp], na[kGp], nb[kGp];
+#pragma unroll
+    for (int q = 0; q < kGp; ++q) {
+        const int i = wrow(q);
+        const bool st = q < r;
+        ca[q] = q < steps ? __ldg((st ? D : LLD) + i) : 0.0;
+        cb[q] = q < steps ? __ldg((st ? LLD : D) + i) : 0.0;
+    }
+    for (int k0 = 0; k0 < steps; k0 += kGp) {
+        {
+            const int kp = min(k0 + kPrefetch, steps - 1);
+            const int ipf = wrow(kp);
+            pf_l2(D + ipf);
+            pf_l2(LLD + ipf);
+        }
+#pragma unroll
+        for (int q = 0; q < kGp; ++q) {
+            const int kk = k0 + kGp + q;
+            const int i = wrow(kk);
+            const bool st = kk < r;
+            na[q] = kk < steps ? __ldg((st ? D : LLD) + i) : 0.0;
+            nb[q] = kk < steps ? __ldg((st ? LLD : D) + i) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kGp; ++q) {
+            const int k = k0 + q;
+            if (k < steps) {
+                const bool st = k < r;
+                const int i = wrow(k);
+                A[st ? i : i + 1] = X;
+                if (dneeds_rescale(X)) {
+                    const double f = dpow2(dscale_exp(X));
+                    X *= f;
+                    Y *= f;
+                }
+                const double t = cb[q] * Y;
+                X = fma(ca[q], X, Y);
+                const unsigned h = (unsigned)__double2hiint(X);
+                neg += (int)((h ^ hx) >> 31);
+                hx = h;
+                Y = fma(mlam, X, t);
+                if (k + 1 == r) {  // the stationary rows are done: the progressive chain starts
+                    Xtop = X;
+                    Ytop = Y;
+                    X = 1.0;
+                    Y = __ldg(D + n - 1) - lam;
+                    hx = (unsigned)__double2hiint(X);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kGp; ++q) {
+            ca[q] = na[q];
+            cb[q] = nb[q];
+        }
+    }
+    // the progressive chain ends at R_{r+1} (R_n = 1 for r = n-1)
+    const double gam = Ytop / Xtop + Y / X + lam;
+    neg += dsign(gam);
+    // an overflow leaves the chain non-finite; a vanished pivot at the twist
+    // leaves no finite gamma_r
+    if (dnotnormal(Xtop) | dnotnormal(X) | !dfinite(gam)) return twisted_guarded(rep, n, lam, pivmin, A, B, gamma, imax);
+    // solve: step k computes z_iz, iz = r-1-k downward (k < r), then
+    // iz = k+1 upward; the coefficient is ld_iz downward, ld_{iz-1} upward
+    auto sz = [&](int k) { return k < r ? r - 1 - k : k + 1; };
+    auto sl = [&](int k) { return k < r ? r - 1 - k : k; };
+    A[r] = 1.0;
+    double nrm2 = 1.0;
+    unsigned long long zmax = dabsbits(1.0);
+    int im = r;
+    double f = 1.0 / Xtop;  // w_r
+    const double vr = 1.0 / X;
+#pragma unroll
+    for (int q = 0; q < kGp; ++q) {
+        ca[q] = q < steps ? A[sz(q)] : 0.0;
+        cb[q] = q < steps ? __ldg(LD + sl(q)) : 0.0;
+    }
+    for (int k0 = 0; k0 < steps; k0 += kGp) {
+        {
+            const int kp = min(k0 + kPrefetch, steps - 1);
+            pf_l2(A + sz(kp));
+            pf_l2(LD + sl(kp));
+        }
+#pragma unroll
+        for (int q = 0; q < kGp; ++q) {
+            const int kk = k0 + kGp + q;
+            na[q] = kk < steps ? A[sz(kk)] : 0.0;
+            nb[q] = kk < steps ? __ldg(LD + sl(kk)) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kGp; ++q) {
+            const int k = k0 + q;
+            if (k < steps) {
+                const int iz = sz(k);
+                if (k == r) f = vr;  // the upward walk restarts at v_r
+                f = -(cb[q] * f);
+                if (dneeds_rescale(ca[q])) f *= dpow2(dscale_exp(ca[q]));
+                const double z = f * ca[q];
+                A[iz] = z;
+                nrm2 = fma(z, z, nrm2);
+                const unsigned long long za = dabsbits(z);
+                const bool better = za > zmax || (za == zmax && iz < im);
+                zmax = better ? za : zmax;
+                im = better ? iz : im;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kGp; ++q) {
+            ca[q] = na[q];
+            cb[q] = nb[q];
+        }
+    }
+    *imax = im;
+    TwistResult<double> res;
+    res.r = r;
+    res.neg = neg;
+    res.nrm2 = nrm2;
+    *gamma = gam;
+    return res;
+}
+
 // One twisted-factorization solve at lam for an eigenpair whose scratch
 // arrays A, B (n words each) are contiguous; same results contract as
 // twisted_solve: z in A (z_r = 1), returns r, inertia count and ||z||^2;
@@ -298,7 +519,8 @@ static __device__ __noinline__ TwistResult<double> twisted_guarded(const double*
 // (i)-(ii)).  r_fixed >= 0: the twist index is given (the largest entry of
 // the previous iterate, as e_r then has a large component along the wanted
 // eigenvector), and only rows < r of the stationary and rows > r of the
-// progressive transform are needed -- one pass instead of two.  In both
+// progressive transform are needed -- one pass instead of two, in the
+// projective form of twisted_fixed_proj.  In both
 // cases the inertia of Delta_r = diag(d+_0..d+_{r-1}, gamma_r,
 // w_{r+1}..w_{n-1}) is the Sturm count at lam (Sylvester), used to update
 // the bisection bracket.
@@ -306,6 +528,7 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
                                                                  double pivmin, double* __restrict__ A,
                                                                  double* __restrict__ B, double* gamma, int* imax,
                                                                  int r_fixed = -1) {
+    if (r_fixed >= 0) return twisted_fixed_proj(rep, n, lam, pivmin, A, B, gamma, imax, r_fixed);
     const double* __restrict__ D = rep;
     const double* __restrict__ L = rep + n;
     const double* __restrict__ LD = rep + 2 * n;
@@ -315,7 +538,7 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
     int r;
     double gbest;
     bool bad;
-    if (r_fixed < 0) {
+    {
         // stationary transform, top-down: l+_i -> A, s_i -> B
         double s = stationary_fast(D, L, LD, n - 1, lam, A, B, &neg);
         double dlast = __ldg(D + n - 1) + s;
@@ -366,64 +589,6 @@ __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* 
             for (int k = 0; k < kG; ++k) cur[k] = nxt[k];
         }
         bad = bad || !dfinite(p);
-    } else {
-        // fixed r: rows < r of the stationary transform (l+ -> A) and rows
-        // > r of the progressive one (u -> B, counting the signs of the
-        // pivots w_{i+1}), as one walk of n-1 steps per lane -- r stationary
-        // rows top-down, then n-1-r progressive rows bottom-up -- so lanes
-        // with different r do not diverge.  Both rows have the form
-        // q = 1 / (a + x), m = b q, with (a, b) = (d_i, ld_i) and the update
-        // x = x (m l_i) - lam for the stationary row, (a, b) = (lld_i, d_i)
-        // and x = x m - lam for the progressive one.
-        r = r_fixed;
-        const double dlast = __ldg(D + n - 1) - lam;
-        double x = -lam, s_r = 0.0;
-        if (r == 0) {
-            s_r = x;
-            x = dlast;
-        }
-        bool st = 0 < r;
-        int i = st ? 0 : n - 2;
-        double a = __ldg((st ? D : LLD) + i), b = __ldg((st ? LD : D) + i), l = __ldg(L + i);
-        for (int k = 0; k < n - 1; ++k) {
-            const int ic = i;
-            const bool stc = st;
-            const double ac = a, bc = b, lc = l;
-            // operands of the next step, one step ahead; their lines
-            // kPrefetch steps ahead into L2
-            {
-                const int kp = min(k + kPrefetch, n - 2);
-                const bool sp = kp < r;
-                const int ipf = sp ? kp : n - 2 - (kp - r);
-                pf_l2((sp ? D : LLD) + ipf);
-                pf_l2((sp ? LD : D) + ipf);
-                pf_l2(L + ipf);
-            }
-            const int k1 = k + 1;
-            st = k1 < r;
-            i = st ? k1 : n - 2 - (k1 - r);
-            if (k1 < n - 1) {
-                a = __ldg((st ? D : LLD) + i);
-                b = __ldg((st ? LD : D) + i);
-                l = __ldg(L + i);
-            }
-            const double den = ac + x;
-            neg += dsign(den);
-            const double m = bc * drcp<2>(den);
-            const double ml = m * lc;
-            *((stc ? A : B) + ic) = stc ? m : ml;
-            x = fma(x, stc ? ml : m, -lam);
-            if (k1 == r) {
-                s_r = x;
-                x = dlast;
-            }
-        }
-        // the switch after row r-1 has run for every r >= 1 (for r = n-1 at
-        // the last step, leaving p_{n-1} = d_{n-1} - lam)
-        const double p = x;
-        gbest = s_r + p + lam;
-        neg += dsign(gbest);
-        bad = !dfinite(s_r) || !dfinite(p) || !dfinite(gbest);
     }
     if (bad) return twisted_guarded(rep, n, lam, pivmin, A, B, gamma, imax);
     res.nrm2 = solve_twisted_fast(LD, n, r, A, B, imax);

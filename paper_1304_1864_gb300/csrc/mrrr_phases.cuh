@@ -337,6 +337,16 @@ MRRR_HD int count_at(const Y* D, const Y* LLD, int n, Y tau, Y pm) {
     return negcount<Y>(D, LLD, n, tau, pm);
 }
 
+// Multisection: kMS lanes per item evaluate the count at kMS equispaced
+// interior points of the same bracket in one sweep, so each sweep divides
+// the bracket into kMS + 1 parts instead of two.  The sweeps are sequential
+// in the row index, so this trades spare throughput for latency.  (Wider
+// sweeps and points at equal ratios shorten the approximation but leave the
+// RQI with brackets from which more eigenpairs need a third step; four
+// equispaced points measured best overall.)
+constexpr int kMS = 4;
+MRRR_HD double ms_point(double lo, double hi, int q) { return lo + (hi - lo) / (kMS + 1) * (q + 1); }
+
 // Bisection for eigenvalue j (1-based) of the rep on the bracket [lo, hi]
 // (Algorithm 1, lines 3 and 16; Sec. 2, "Classification of the
 // eigenvalues"): stop when hi - lo <= max(rtol max(|lo|, |hi|), 2 pivmin).
@@ -816,13 +826,13 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     const double tol = cfg.mixed ? cfg.krs * gap * cfg.eps_x * sq : cfg.krs * gap * n * cfg.eps_y / cfg.gaptol;
     Y lo = from_d<Y>(I.lo), hi = from_d<Y>(I.hi);
     if (std::is_same<Y, double>::value && I.rqi_done == 0) {
-        // the bracket was verified by the tuned binary64 count, whose
-        // reciprocal has one Newton step: it is exact for the rep perturbed
-        // element-wise by ~2^-44, so its eigenvalues can sit ~n 2^-44 |lambda|
-        // from the ones the full-precision steps below converge to.  Widen the
-        // safeguard by that much so a correct Rayleigh correction near an end
-        // is not rejected as leaving the bracket (the inertia of the first
-        // step narrows it again).
+        // the bracket was verified by the tuned binary64 count, which is exact
+        // for the rep perturbed element-wise by a few ulps, so its eigenvalues
+        // can sit ~n ulps |lambda| from the ones the steps below converge to
+        // (rounded in another order).  Widen the safeguard by a generous
+        // multiple of that so a correct Rayleigh correction near an end is not
+        // rejected as leaving the bracket (the inertia of the first step
+        // narrows it again).
         const double pad = 16.0 * n * 0x1p-44 * fmax(fabs(I.lo), fabs(I.hi)) + 4.0 * B.pivmin;
         lo = from_d<Y>(I.lo - pad);
         hi = from_d<Y>(I.hi + pad);

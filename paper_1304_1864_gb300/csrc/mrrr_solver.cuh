@@ -274,20 +274,52 @@ __global__ void k_bisect_lo(Item* items, const int* list, int count, const Block
     if (s) atomicAdd(&C->qd_steps_low, s);
 }
 
-// Multisection variant of the low-precision pre-bisection: kMS lanes per
-// item evaluate the count at kMS interior points of the same bracket in one
-// sweep, so each sweep gains log2(kMS + 1) bits instead of one.  The sweeps
-// are sequential in the row index, so this trades spare low-precision
-// throughput for latency.  Lanes of one item are adjacent in a warp and share
-// their counts by shuffles; every lane of the group keeps the same bracket.
-constexpr int kMS = 4;
+// Multisection sweeps (kMS, ms_point) with the lanes of one item adjacent in
+// a warp, sharing their counts by shuffles.
+
+// shuffle mask of the kMS-lane group of this thread
+__device__ __forceinline__ unsigned ms_mask() {
+    return ((1u << kMS) - 1u) << ((threadIdx.x & 31) & ~(kMS - 1));
+}
+
+// Given the counts c_k at the points x_k (k < kMS) of a sweep, in increasing
+// order: the first point whose count reaches j is the new upper end and the
+// point before it the new lower end -- well defined even where rounding makes
+// a count non-monotone.  Points that rounded onto or outside the bracket are
+// skipped.  Returns false when no point was inside.
+__device__ __forceinline__ bool ms_update(unsigned mask, int c, double x, bool inside, int j, double& lo, double& hi) {
+    double nlo = lo, nhi = hi;
+    bool any_inside = false, found = false;
+#pragma unroll
+    for (int k = 0; k < kMS; ++k) {
+        const int ck = __shfl_sync(mask, c, k, kMS);
+        const double xk = __shfl_sync(mask, x, k, kMS);
+        const bool ik = __shfl_sync(mask, (int)inside, k, kMS) != 0;
+        any_inside |= ik;
+        if (!ik || found) continue;
+        if (ck >= j) {
+            nhi = xk;
+            found = true;
+        } else {
+            nlo = xk;
+        }
+    }
+    if (!any_inside) return false;
+    lo = nlo;
+    hi = nhi;
+    return true;
+}
+
+// Low-precision pre-bisection of the listed items (Sec. 3.2: eigenvalues are
+// approximated in a precision below the working one) down to a relative
+// width wrel, by multisection with kMS lanes per item.
 template <class Lo>
 __global__ void k_bisect_lo_ms(Item* items, const int* list, int count, const BlockDesc* blocks, double wrel,
                                DevCounters* C) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int g = t / kMS, q = t % kMS;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = t / kMS, q = t % kMS;
     if (g >= count) return;  // whole groups leave together (kMS divides 32)
-    unsigned mask = ((1u << kMS) - 1u) << ((threadIdx.x & 31) & ~(kMS - 1));
+    const unsigned mask = ms_mask();
     Item& I = items[list ? list[g] : g];
     const int n = I.n;
     if (n == 1) return;
@@ -298,57 +330,31 @@ __global__ void k_bisect_lo_ms(Item* items, const int* list, int count, const Bl
     unsigned long long steps = 0;
     for (int it = 0; it < 64; ++it) {
         if (!(hi - lo > wrel * fmax(fabs(lo), fabs(hi)))) break;
-        double w = (hi - lo) / (kMS + 1);
-        Lo x = (Lo)(lo + w * (q + 1));
-        bool inside = (double)x > lo && (double)x < hi;
-        int c = inside ? negcount_lo<Lo>(D, LLD, n, x, pm) : (q < kMS / 2 ? -1 : n + 1);
+        const Lo x = (Lo)ms_point(lo, hi, q);
+        const bool inside = (double)x > lo && (double)x < hi;
+        const int c = inside ? negcount_lo<Lo>(D, LLD, n, x, pm) : 0;
         if (inside) steps += (unsigned long long)n;
-        // the first point (left to right) whose count reaches j is the new
-        // upper end and the point before it the new lower end -- well defined
-        // even where rounding makes the low-precision count non-monotone
-        double nlo = lo, nhi = hi;
-        bool any_inside = false, found = false;
-#pragma unroll
-        for (int k = 0; k < kMS; ++k) {
-            int ck = __shfl_sync(mask, c, k, kMS);
-            double xk = __shfl_sync(mask, (double)x, k, kMS);
-            bool ik = __shfl_sync(mask, (int)inside, k, kMS) != 0;
-            any_inside |= ik;
-            if (!ik || found) continue;
-            if (ck >= I.j) {
-                nhi = xk;
-                found = true;
-            } else {
-                nlo = xk;
-            }
-        }
-        if (!any_inside) break;  // no representable interior point left
-        lo = nlo;
-        hi = nhi;
+        if (!ms_update(mask, c, (double)x, inside, I.j, lo, hi)) break;  // no representable interior point left
     }
     if (q == 0) {
         I.lo = lo;
         I.hi = hi;
-        if (steps) atomicAdd(&C->qd_steps_low, steps);
-    } else if (steps) {
-        atomicAdd(&C->qd_steps_low, steps);
     }
+    if (steps) atomicAdd(&C->qd_steps_low, steps);
 }
 
 // Working-precision refinement of the listed items by multisection (the
-// same kMS-point sweeps as k_bisect_lo_ms, with the count of the working
-// precision): down to hi - lo <= max(rtol max(|lo|, |hi|), 2 pivmin), as
-// bisect_bracket.  The refinement starts from verified brackets a few bits
-// wide, so two sweeps replace about five sequential bisection steps, and the
-// kMS lanes per item put four times as many warps on the FP64 pipes.  The
-// list length is read on the device.
+// same sweeps as k_bisect_lo_ms, with the count of the working precision):
+// down to hi - lo <= max(rtol max(|lo|, |hi|), 2 pivmin), as bisect_bracket.
+// The refinement starts from verified brackets a few bits wide.  The list
+// length is read on the device.
 template <class Y>
 __global__ void k_bisect_ms(Item* items, const int* list, const int* count_dev, int bound, const BlockDesc* blocks,
                             double rtol, unsigned long long* step_counter) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int g = t / kMS, q = t % kMS;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = t / kMS, q = t % kMS;
     if (g >= bound || g >= *count_dev) return;  // whole groups leave together (kMS divides 32)
-    unsigned mask = ((1u << kMS) - 1u) << ((threadIdx.x & 31) & ~(kMS - 1));
+    const unsigned mask = ms_mask();
     Item& I = items[list[g]];
     const int n = I.n;
     if (n == 1) {
@@ -365,34 +371,13 @@ __global__ void k_bisect_ms(Item* items, const int* list, const int* count_dev, 
     double lo = I.lo, hi = I.hi;
     unsigned long long steps = 0;
     for (int it = 0; it < 64; ++it) {
-        double tol = fmax(rtol * fmax(fabs(lo), fabs(hi)), 2.0 * pivmin);
+        const double tol = fmax(rtol * fmax(fabs(lo), fabs(hi)), 2.0 * pivmin);
         if (!(tol < hi - lo)) break;
-        double w = (hi - lo) / (kMS + 1);
-        double x = lo + w * (q + 1);
-        bool inside = x > lo && x < hi;
-        int c = inside ? count_at<Y, true>(D, LLD, n, from_d<Y>(x), pm) : (q < kMS / 2 ? -1 : n + 1);
+        const double x = ms_point(lo, hi, q);
+        const bool inside = x > lo && x < hi;
+        const int c = inside ? count_at<Y, true>(D, LLD, n, from_d<Y>(x), pm) : 0;
         if (inside) steps += (unsigned long long)n;
-        // first point (left to right) whose count reaches j: new upper end;
-        // the point before it: new lower end
-        double nlo = lo, nhi = hi;
-        bool any_inside = false, found = false;
-#pragma unroll
-        for (int k = 0; k < kMS; ++k) {
-            int ck = __shfl_sync(mask, c, k, kMS);
-            double xk = __shfl_sync(mask, x, k, kMS);
-            bool ik = __shfl_sync(mask, (int)inside, k, kMS) != 0;
-            any_inside |= ik;
-            if (!ik || found) continue;
-            if (ck >= I.j) {
-                nhi = xk;
-                found = true;
-            } else {
-                nlo = xk;
-            }
-        }
-        if (!any_inside) break;
-        lo = nlo;
-        hi = nhi;
+        if (!ms_update(mask, c, x, inside, I.j, lo, hi)) break;
     }
     if (q == 0) {
         I.lo = lo;
@@ -917,6 +902,10 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 }
             }
             tl.end(nz);
+            int num_sms = 0, dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms < 1)
+                num_sms = 152;
             // a3: initial eigenvalues (Algorithm 1, line 3): low-precision
             // pre-bisection, verification of both bracket ends and refinement of
             // the items not yet certified, in the working precision
@@ -925,8 +914,8 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 tl.begin(phase);
                 int launches = 0;
                 if (use_low) {
-                    k_bisect_lo_ms<Lo><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(items, list, count,
-                                                                                          d_blocks, wrel_lo, d_C);
+                    k_bisect_lo_ms<Lo><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(
+                        items, list, count, d_blocks, wrel_lo, d_C);
                     MRRR_CK(cudaMemsetAsync(&d_C->nvfix, 0, sizeof(int), st));
                     k_verify<Y><<<grid_for(2LL * count, kLatThreads), kLatThreads, 0, st>>>(
                         items, list, count, d_blocks, d_C, ctr, vflags, vfix_list);
@@ -952,10 +941,6 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             tl.end();
             MRRR_CK(cudaGetLastError());
             size_t per = 2 * (size_t)nmax * sizeof(Y);
-            int num_sms = 0, dev = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms < 1)
-                num_sms = 152;
             // RQI in passes: two steps per eigenpair in the first pass (most
             // converge), then the parked ones, densely packed, in further
             // passes; the last pass has the rest of the max_rqi budget
