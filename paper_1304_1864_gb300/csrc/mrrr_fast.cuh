@@ -144,6 +144,72 @@ __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const
     return cnt;
 }
 
+// The low-precision Sturm count of the pre-bisection (binary32 under a
+// binary64 working precision, see negcount_lo) in the same projective form
+// as negcount_fast: two dependent FMAs per row instead of an add, a divide
+// and a subtract.  binary32 has a narrower exponent range, so the pair is
+// rescaled every eight rows; an overflow (non-finite P or N) falls back to
+// the divide form.  Its brackets are verified in the working precision.
+static __device__ __noinline__ int negcount_lo_guarded(const float* D, const float* LLD, int n, float tau,
+                                                       float pivmin) {
+    return negcount_lo<float>(D, LLD, n, tau, pivmin);
+}
+
+__device__ __forceinline__ int negcount_lo_fast(const float* __restrict__ D, const float* __restrict__ LLD, int n,
+                                                float tau, float pivmin) {
+    const float mtau = -tau;
+    float P = 1.0f, N = mtau;
+    unsigned hp = 0u;  // bits of P_{i-1}
+    int cnt = 0;
+    int i = 0;
+    for (; i + 8 <= n - 1; i += 8) {
+        const int ip = min(i + kPrefetch, n - 1);
+        pf_l2(D + ip);
+        pf_l2(LLD + ip);
+        float d[8], l[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            d[k] = __ldg(D + i + k);
+            l[k] = __ldg(LLD + i + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float a = l[k] * N;
+            P = fmaf(d[k], P, N);
+            const unsigned h = __float_as_uint(P);
+            cnt += (int)((h ^ hp) >> 31);
+            hp = h;
+            N = fmaf(mtau, P, a);
+        }
+        // scale by 2^k with |P| 2^k in [1, 2), k clamped so that 2^k is normal
+        const int e = (int)((hp >> 23) & 0xffu);
+        const int k = max(127 - e, -126);
+        const float f = __uint_as_float((unsigned)(k + 127) << 23);
+        P *= f;
+        N *= f;
+    }
+    for (; i < n - 1; ++i) {
+        const float a = __ldg(LLD + i) * N;
+        P = fmaf(__ldg(D + i), P, N);
+        const unsigned h = __float_as_uint(P);
+        cnt += (int)((h ^ hp) >> 31);
+        hp = h;
+        N = fmaf(mtau, P, a);
+    }
+    P = fmaf(__ldg(D + n - 1), P, N);
+    cnt += (int)((__float_as_uint(P) ^ hp) >> 31);
+    if (!isfinite(P) || !isfinite(N)) return negcount_lo_guarded(D, LLD, n, tau, pivmin);
+    return cnt;
+}
+
+// Pre-bisection count for the low precision Lo of the device path
+template <class Lo>
+__device__ __forceinline__ int count_lo(const Lo* D, const Lo* LLD, int n, Lo tau, Lo pivmin) {
+    if constexpr (std::is_same<Lo, float>::value) return negcount_lo_fast(D, LLD, n, tau, pivmin);
+    else if constexpr (std::is_same<Lo, double>::value) return negcount_fast(D, LLD, n, tau, pivmin);
+    else return negcount_lo<Lo>(D, LLD, n, tau, pivmin);
+}
+
 // Stationary transform on rows [0, m): l+_i -> A[i] and, if B != nullptr,
 // s_i -> B[i].  Returns s_m; *neg += number of negative d+_i, i < m.
 __device__ __forceinline__ double stationary_fast(const double* __restrict__ D, const double* __restrict__ L,

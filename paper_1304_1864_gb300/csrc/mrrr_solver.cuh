@@ -332,7 +332,7 @@ __global__ void k_bisect_lo_ms(Item* items, const int* list, int count, const Bl
         if (!(hi - lo > wrel * fmax(fabs(lo), fabs(hi)))) break;
         const Lo x = (Lo)ms_point(lo, hi, q);
         const bool inside = (double)x > lo && (double)x < hi;
-        const int c = inside ? negcount_lo<Lo>(D, LLD, n, x, pm) : 0;
+        const int c = inside ? count_lo<Lo>(D, LLD, n, x, pm) : 0;
         if (inside) steps += (unsigned long long)n;
         if (!ms_update(mask, c, (double)x, inside, I.j, lo, hi)) break;  // no representable interior point left
     }
