@@ -2,12 +2,13 @@
 
 Workload (one step): the three n = 4001 tridiagonals of the mixed
 single/double configuration -- 1-2-1 Toeplitz, Wilkinson W_4001 and Clement --
-float32 in/out with binary64 internals, all eigenpairs, each matrix solved on
-its own by one mrrr_solve_s call (the three calls run concurrently on three
-streams).  Inputs are resident on the device; L2 is flushed (256 MiB write)
-between timed steps.  Also reported: the same step as sequential solves and
-as one batched call, the 4096-matrix batched workload, the double-double
-glued-Wilkinson solve and a bounded replay of the serving trace.
+float32 in/out with binary64 internals, all eigenpairs, the three matrices in
+one mrrr_solve_batch_s call (each solved on its own, Algorithm 1 per matrix,
+in one sequence of launches).  Inputs are resident on the device; L2 is
+flushed (256 MiB write) between timed steps.  Also reported: the same step as
+three sequential and as three concurrent mrrr_solve_s calls, the 4096-matrix
+batched workload, the double-double glued-Wilkinson solve and a bounded
+replay of the serving trace.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank solves its own copy of the workload (weak scaling,
@@ -41,7 +42,7 @@ PHASE_KERNEL = {"bisect": "k_bisect", "refine": "k_bisect", "rqi": "k_rqi", "shi
 # DRAM bytes (read + write) per k_rqi launch on this workload, the mean over the
 # launches of one `ncu --set full` capture; valid only while the sources that
 # define the kernel hash to the value they had at the capture
-RQI_TRAFFIC = {"bytes_per_launch": 404.7e6, "sources_sha1": "7fe9c0f570013d00d8ffbf5a310589ee91b87443",
+RQI_TRAFFIC = {"bytes_per_launch": 957.4e6, "sources_sha1": "8611b5325d148f191249a9339d02f7bf810f6030",
                "sources": ("mrrr_core.cuh", "mrrr_dd.cuh", "mrrr_fast.cuh", "mrrr_phases.cuh", "mrrr_solver.cuh",
                            "mrrr_types.cuh", "solver_s.cu")}
 
@@ -276,6 +277,20 @@ class _Solo:
         return [dict(st) for st in self.stats]
 
 
+class _Batch:
+    """The C2 step: the three matrices in one mrrr_solve_batch_s call (each
+    matrix solved on its own, Algorithm 1 per matrix, in one sequence of
+    launches over all of them), on the caller's stream."""
+
+    def __init__(self, m, mats):
+        self.m, self.mats = m, mats
+
+    def run(self, timing=False):
+        out, st, status = self.m.solve_batch(self.mats, mode="mixed", timing=timing, check=False)
+        assert all(s == 0 for s in status), status
+        return [dict(st)]
+
+
 def _time_steps(fn, steps, dev, flush):
     """Device time (ms) of `steps` calls of fn(), an L2 flush before each;
     returns (total ms, results)."""
@@ -313,15 +328,15 @@ def run_ours(args):
     mats = [(torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev)) for d, e in mats_h]
     pairs_per_step = sum(d.shape[0] for d, _ in mats_h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    solo = _Solo(m, mats, dev)
+    step = _Batch(m, mats)
     for _ in range(args.warmup):
-        solo.run()
+        step.run()
     torch.cuda.synchronize(dev)
     _barrier(world)
     with ClockSampler(dev.index) as clk:
         torch.cuda.synchronize(dev)
         _barrier(world)
-        ms_total, outs = _time_steps(lambda: solo.run(timing=True), args.steps, dev, flush)
+        ms_total, outs = _time_steps(lambda: step.run(timing=True), args.steps, dev, flush)
         torch.cuda.synchronize(dev)
         _barrier(world)
     acc = {}
@@ -367,12 +382,12 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "mode": "mixed single/double (fp32 io, fp64 internals)",
-                           "solves": "each matrix solved on its own: 3 mrrr_solve_s calls issued concurrently "
-                                     "on 3 CUDA streams from 3 host threads",
+                           "solves": "the 3 matrices in one mrrr_solve_batch_s call: each matrix solved on its "
+                                     "own (Algorithm 1 per matrix) in one sequence of launches over all of them",
                            "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replica per GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(),
-                "tree": {nm: [st[key] for st in last] for nm, key in
+                "tree": {nm: last[0][key] for nm, key in
                          (("d_max", "d_max"), ("clusters", "nclusters"), ("largest_cluster", "largest_cluster"),
                           ("reps_failed", "reps_failed"), ("rqi_iters", "rqi_iters"), ("fallbacks", "fallbacks"))}}
         line["variants"] = _variants(m, mats, args, dev, flush)
@@ -393,8 +408,8 @@ def run_ours(args):
 
 
 def _variants(m, mats, args, dev, flush):
-    """The same C2 step issued as three sequential solves and as one batched
-    call (mrrr_solve_batch_s)."""
+    """The same C2 step issued as three sequential mrrr_solve_s calls and as
+    three concurrent ones (three streams, three host threads)."""
     import torch
     pairs = sum(d.shape[0] for d, _ in mats)
     res = {}
@@ -403,11 +418,9 @@ def _variants(m, mats, args, dev, flush):
         for d, e in mats:
             m.solve(d, e, mode="mixed", check=True)
 
-    def bat():
-        out, st, status = m.solve_batch(mats, mode="mixed")
-        assert all(s == 0 for s in status), status
+    solo = _Solo(m, mats, dev)
 
-    for label, fn in (("sequential_solves", seq), ("one_batched_call", bat)):
+    for label, fn in (("sequential_solves", seq), ("concurrent_solves", solo.run)):
         fn()
         torch.cuda.synchronize(dev)
         ms, _ = _time_steps(fn, args.steps, dev, flush)
