@@ -454,61 +454,65 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
     double X = 1.0, Y = r > 0 ? mlam : __ldg(D + n - 1) - lam;
     double Xtop = 1.0, Ytop = mlam;
     unsigned hx = (unsigned)__double2hiint(X);
+    // steps in whole groups of kGp (their operands loaded a group ahead,
+    // with no per-step bounds test), then the remaining steps
+    const int full = steps - steps % kGp;
+    auto wstep = [&](int k, double a, double b) {
+        const bool st = k < r;
+        const int i = wrow(k);
+        A[st ? i : i + 1] = X;
+        if (dneeds_rescale(X)) {
+            const double f = dpow2(dscale_exp(X));
+            X *= f;
+            Y *= f;
+        }
+        const double t = b * Y;
+        X = fma(a, X, Y);
+        const unsigned h = (unsigned)__double2hiint(X);
+        neg += (int)((h ^ hx) >> 31);
+        hx = h;
+        Y = fma(mlam, X, t);
+        if (k + 1 == r) {  // the stationary rows are done: the progressive chain starts
+            Xtop = X;
+            Ytop = Y;
+            X = 1.0;
+            Y = __ldg(D + n - 1) - lam;
+            hx = (unsigned)__double2hiint(X);
+        }
+    };
+    // operands of walk step k (clamped to a valid row past the end)
+    auto wload = [&](int k, double& a, double& b) {
+        const int kc = min(k, steps - 1);
+        const int i = wrow(kc);
+        const bool st = kc < r;
+        a = __ldg((st ? D : LLD) + i);
+        b = __ldg((st ? LLD : D) + i);
+    };
     double ca[kGp], cb[kGp], na[kGp], nb[kGp];
+    if (full > 0) {
 #pragma unroll
-    for (int q = 0; q < kGp; ++q) {
-        const int i = wrow(q);
-        const bool st = q < r;
-        ca[q] = q < steps ? __ldg((st ? D : LLD) + i) : 0.0;
-        cb[q] = q < steps ? __ldg((st ? LLD : D) + i) : 0.0;
+        for (int q = 0; q < kGp; ++q) wload(q, ca[q], cb[q]);
     }
-    for (int k0 = 0; k0 < steps; k0 += kGp) {
+    for (int k0 = 0; k0 < full; k0 += kGp) {
         {
-            const int kp = min(k0 + kPrefetch, steps - 1);
-            const int ipf = wrow(kp);
+            const int ipf = wrow(min(k0 + kPrefetch, steps - 1));
             pf_l2(D + ipf);
             pf_l2(LLD + ipf);
         }
 #pragma unroll
-        for (int q = 0; q < kGp; ++q) {
-            const int kk = k0 + kGp + q;
-            const int i = wrow(kk);
-            const bool st = kk < r;
-            na[q] = kk < steps ? __ldg((st ? D : LLD) + i) : 0.0;
-            nb[q] = kk < steps ? __ldg((st ? LLD : D) + i) : 0.0;
-        }
+        for (int q = 0; q < kGp; ++q) wload(k0 + kGp + q, na[q], nb[q]);
 #pragma unroll
-        for (int q = 0; q < kGp; ++q) {
-            const int k = k0 + q;
-            if (k < steps) {
-                const bool st = k < r;
-                const int i = wrow(k);
-                A[st ? i : i + 1] = X;
-                if (dneeds_rescale(X)) {
-                    const double f = dpow2(dscale_exp(X));
-                    X *= f;
-                    Y *= f;
-                }
-                const double t = cb[q] * Y;
-                X = fma(ca[q], X, Y);
-                const unsigned h = (unsigned)__double2hiint(X);
-                neg += (int)((h ^ hx) >> 31);
-                hx = h;
-                Y = fma(mlam, X, t);
-                if (k + 1 == r) {  // the stationary rows are done: the progressive chain starts
-                    Xtop = X;
-                    Ytop = Y;
-                    X = 1.0;
-                    Y = __ldg(D + n - 1) - lam;
-                    hx = (unsigned)__double2hiint(X);
-                }
-            }
-        }
+        for (int q = 0; q < kGp; ++q) wstep(k0 + q, ca[q], cb[q]);
 #pragma unroll
         for (int q = 0; q < kGp; ++q) {
             ca[q] = na[q];
             cb[q] = nb[q];
         }
+    }
+    for (int k = full; k < steps; ++k) {
+        double a, b;
+        wload(k, a, b);
+        wstep(k, a, b);
     }
     // the progressive chain ends at R_{r+1} (R_n = 1 for r = n-1)
     const double gam = Ytop / Xtop + Y / X + lam;
@@ -517,7 +521,10 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
     // leaves no finite gamma_r
     if (dnotnormal(Xtop) | dnotnormal(X) | !dfinite(gam)) return twisted_guarded(rep, n, lam, pivmin, A, B, gamma, imax);
     // solve: step k computes z_iz, iz = r-1-k downward (k < r), then
-    // iz = k+1 upward; the coefficient is ld_iz downward, ld_{iz-1} upward
+    // iz = k+1 upward; the coefficient is ld_iz downward, ld_{iz-1} upward.
+    // The arg-max of |z| (smallest index on ties) is exact: it is the next
+    // twist index and also fixes the sign of the stored vector (largest entry
+    // positive).
     auto sz = [&](int k) { return k < r ? r - 1 - k : k + 1; };
     auto sl = [&](int k) { return k < r ? r - 1 - k : k; };
     A[r] = 1.0;
@@ -526,45 +533,48 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
     int im = r;
     double f = 1.0 / Xtop;  // w_r
     const double vr = 1.0 / X;
+    auto sstep = [&](int k, double a, double l) {
+        const int iz = sz(k);
+        if (k == r) f = vr;  // the upward walk restarts at v_r
+        f = -(l * f);
+        if (dneeds_rescale(a)) f *= dpow2(dscale_exp(a));
+        const double z = f * a;
+        A[iz] = z;
+        nrm2 = fma(z, z, nrm2);
+        const unsigned long long za = dabsbits(z);
+        const bool better = za > zmax || (za == zmax && iz < im);
+        zmax = better ? za : zmax;
+        im = better ? iz : im;
+    };
+    auto sload = [&](int k, double& a, double& l) {
+        const int kc = min(k, steps - 1);
+        a = A[sz(kc)];
+        l = __ldg(LD + sl(kc));
+    };
+    if (full > 0) {
 #pragma unroll
-    for (int q = 0; q < kGp; ++q) {
-        ca[q] = q < steps ? A[sz(q)] : 0.0;
-        cb[q] = q < steps ? __ldg(LD + sl(q)) : 0.0;
+        for (int q = 0; q < kGp; ++q) sload(q, ca[q], cb[q]);
     }
-    for (int k0 = 0; k0 < steps; k0 += kGp) {
+    for (int k0 = 0; k0 < full; k0 += kGp) {
         {
             const int kp = min(k0 + kPrefetch, steps - 1);
             pf_l2(A + sz(kp));
             pf_l2(LD + sl(kp));
         }
 #pragma unroll
-        for (int q = 0; q < kGp; ++q) {
-            const int kk = k0 + kGp + q;
-            na[q] = kk < steps ? A[sz(kk)] : 0.0;
-            nb[q] = kk < steps ? __ldg(LD + sl(kk)) : 0.0;
-        }
+        for (int q = 0; q < kGp; ++q) sload(k0 + kGp + q, na[q], nb[q]);
 #pragma unroll
-        for (int q = 0; q < kGp; ++q) {
-            const int k = k0 + q;
-            if (k < steps) {
-                const int iz = sz(k);
-                if (k == r) f = vr;  // the upward walk restarts at v_r
-                f = -(cb[q] * f);
-                if (dneeds_rescale(ca[q])) f *= dpow2(dscale_exp(ca[q]));
-                const double z = f * ca[q];
-                A[iz] = z;
-                nrm2 = fma(z, z, nrm2);
-                const unsigned long long za = dabsbits(z);
-                const bool better = za > zmax || (za == zmax && iz < im);
-                zmax = better ? za : zmax;
-                im = better ? iz : im;
-            }
-        }
+        for (int q = 0; q < kGp; ++q) sstep(k0 + q, ca[q], cb[q]);
 #pragma unroll
         for (int q = 0; q < kGp; ++q) {
             ca[q] = na[q];
             cb[q] = nb[q];
         }
+    }
+    for (int k = full; k < steps; ++k) {
+        double a, l;
+        sload(k, a, l);
+        sstep(k, a, l);
     }
     *imax = im;
     TwistResult<double> res;
