@@ -42,7 +42,7 @@ PHASE_KERNEL = {"bisect": "k_bisect", "refine": "k_bisect", "rqi": "k_rqi", "shi
 # DRAM bytes (read + write) per k_rqi launch on this workload, the mean over the
 # launches of one `ncu --set full` capture; valid only while the sources that
 # define the kernel hash to the value they had at the capture
-RQI_TRAFFIC = {"bytes_per_launch": 957.4e6, "sources_sha1": "8611b5325d148f191249a9339d02f7bf810f6030",
+RQI_TRAFFIC = {"bytes_per_launch": 952.5e6, "sources_sha1": "dfe7dd43094dc9917bbfb2d774607aca8924c2bd",
                "sources": ("mrrr_core.cuh", "mrrr_dd.cuh", "mrrr_fast.cuh", "mrrr_phases.cuh", "mrrr_solver.cuh",
                            "mrrr_types.cuh", "solver_s.cu")}
 
