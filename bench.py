@@ -42,7 +42,7 @@ PHASE_KERNEL = {"bisect": "k_bisect", "refine": "k_bisect", "rqi": "k_rqi", "shi
 # DRAM bytes (read + write) per k_rqi launch on this workload, the mean over the
 # launches of one `ncu --set full` capture; valid only while the sources that
 # define the kernel hash to the value they had at the capture
-RQI_TRAFFIC = {"bytes_per_launch": 952.5e6, "sources_sha1": "dfe7dd43094dc9917bbfb2d774607aca8924c2bd",
+RQI_TRAFFIC = {"bytes_per_launch": 957.5e6, "sources_sha1": "f3d9c7e46fcc1075247d9a306e54fe13a65897d2",
                "sources": ("mrrr_core.cuh", "mrrr_dd.cuh", "mrrr_fast.cuh", "mrrr_phases.cuh", "mrrr_solver.cuh",
                            "mrrr_types.cuh", "solver_s.cu")}
 

@@ -96,14 +96,17 @@ __device__ __forceinline__ bool dneeds_rescale(double x) {
 // (after preprocessing a row changes |P| by a pivot of modest size).  A
 // vanished pivot needs no special case: P_i = +-0 counts d+_i as a pivot of
 // that sign and the recurrence continues from N_{i+1} = lld_i N_i (the limit
-// of the divide form); only an overflow, which leaves P or N non-finite,
-// sends the count to the guarded divide form.
+// of the divide form).  An overflow, or an underflow that leaves P zero or
+// subnormal at a rescaling point (where the pair could have vanished
+// altogether and lost the count), sends the count to the guarded divide
+// form.
 __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const double* __restrict__ LLD, int n,
                                              double tau, double pivmin) {
     const double mtau = -tau;
     double P = 1.0, N = mtau;
     unsigned hp = 0u;  // high word of P_{i-1}
     int cnt = 0;
+    unsigned bad = 0u;
     int i = 0;
     for (; i + 8 <= n - 1; i += 8) {
         const int ip = min(i + kPrefetch, n - 1);
@@ -125,6 +128,7 @@ __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const
             N = fma(mtau, P, a);
         }
         if (i & 8) {  // every sixteen rows (the same rows in every lane)
+            bad |= dnotnormal(P);
             const double f = dpow2(dscale_exp(P));
             P *= f;
             N *= f;
@@ -140,7 +144,7 @@ __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const
     }
     P = fma(__ldg(D + n - 1), P, N);
     cnt += (int)((((unsigned)__double2hiint(P)) ^ hp) >> 31);
-    if (!dfinite(P) || !dfinite(N)) return negcount_guarded(D, LLD, n, tau, pivmin);
+    if (bad | dnotnormal(P) | !dfinite(N)) return negcount_guarded(D, LLD, n, tau, pivmin);
     return cnt;
 }
 
@@ -148,8 +152,9 @@ __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const
 // binary64 working precision, see negcount_lo) in the same projective form
 // as negcount_fast: two dependent FMAs per row instead of an add, a divide
 // and a subtract.  binary32 has a narrower exponent range, so the pair is
-// rescaled every eight rows; an overflow (non-finite P or N) falls back to
-// the divide form.  Its brackets are verified in the working precision.
+// rescaled every four rows; an overflow, or a P that is zero or subnormal at
+// a rescaling point or at the end, falls back to the divide form.  Its
+// brackets are verified in the working precision.
 static __device__ __noinline__ int negcount_lo_guarded(const float* D, const float* LLD, int n, float tau,
                                                        float pivmin) {
     return negcount_lo<float>(D, LLD, n, tau, pivmin);
@@ -161,6 +166,7 @@ __device__ __forceinline__ int negcount_lo_fast(const float* __restrict__ D, con
     float P = 1.0f, N = mtau;
     unsigned hp = 0u;  // bits of P_{i-1}
     int cnt = 0;
+    unsigned bad = 0u;
     int i = 0;
     for (; i + 8 <= n - 1; i += 8) {
         const int ip = min(i + kPrefetch, n - 1);
@@ -180,13 +186,17 @@ __device__ __forceinline__ int negcount_lo_fast(const float* __restrict__ D, con
             cnt += (int)((h ^ hp) >> 31);
             hp = h;
             N = fmaf(mtau, P, a);
+            if ((k & 3) == 3) {
+                // every four rows: scale by 2^q with |P| 2^q in [1, 2), q
+                // clamped so that 2^q is normal
+                const int e = (int)((hp >> 23) & 0xffu);
+                bad |= (unsigned)(e == 0 || e == 255);
+                const int q = max(127 - e, -126);
+                const float f = __uint_as_float((unsigned)(q + 127) << 23);
+                P *= f;
+                N *= f;
+            }
         }
-        // scale by 2^k with |P| 2^k in [1, 2), k clamped so that 2^k is normal
-        const int e = (int)((hp >> 23) & 0xffu);
-        const int k = max(127 - e, -126);
-        const float f = __uint_as_float((unsigned)(k + 127) << 23);
-        P *= f;
-        N *= f;
     }
     for (; i < n - 1; ++i) {
         const float a = __ldg(LLD + i) * N;
@@ -198,7 +208,9 @@ __device__ __forceinline__ int negcount_lo_fast(const float* __restrict__ D, con
     }
     P = fmaf(__ldg(D + n - 1), P, N);
     cnt += (int)((__float_as_uint(P) ^ hp) >> 31);
-    if (!isfinite(P) || !isfinite(N)) return negcount_lo_guarded(D, LLD, n, tau, pivmin);
+    const unsigned ee = (__float_as_uint(P) >> 23) & 0xffu;
+    if (bad | (unsigned)(ee == 0u || ee == 255u) | (unsigned)!isfinite(N))
+        return negcount_lo_guarded(D, LLD, n, tau, pivmin);
     return cnt;
 }
 
