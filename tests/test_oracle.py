@@ -242,8 +242,6 @@ def _build_mutant(tmp, name):
 
 def _pins_pass(so):
     """Run a subset of the pins against a library built from `so`."""
-    import ctypes
-    import importlib
     import oracle as om
     saved = om._lib
     try:
