@@ -71,6 +71,28 @@ def test_config_n4001_mixed_single_double():
         _acc.check_sign_convention(Z, "s")
 
 
+def test_config_n4001_batched_call():
+    # the benchmark's launch configuration: the three n = 4001 matrices in one
+    # mrrr_solve_batch_s call.  Each matrix's eigenpairs are bit-identical to
+    # its own solve (checked against the oracle above), and sampled
+    # eigenvalues are checked against the oracle directly.
+    import paper_1304_1864_gb300 as m
+    mats_h = inputs.workload_c2()
+    mats = [(torch.tensor(d, dtype=torch.float32, device="cuda"), torch.tensor(e, dtype=torch.float32, device="cuda"))
+            for d, e in mats_h]
+    out, st, status = m.solve_batch(mats, mode="mixed")
+    torch.cuda.synchronize()
+    assert all(s == 0 for s in status), status
+    rng = np.random.default_rng(3)
+    for (d, e), (dg, eg), (Wb, Zb) in zip(mats_h, mats, out):
+        W1, Z1, _ = m.solve(dg, eg, mode="mixed")
+        assert torch.equal(W1, Wb) and torch.equal(Z1, Zb)
+        d64, e64 = _acc.exact_input(d, e, "s")
+        n = d64.size
+        idx = np.unique(np.concatenate([[0, n // 3, n - 1], rng.integers(0, n, 12)]))
+        _acc.check_eigvals(d64, e64, _acc.as_np(Wb), "s", "mixed", idx=idx)
+
+
 def test_121_closed_form_full_size():
     # 1-2-1 at n = 4001: lambda_k = 2 - 2 cos(k pi/(n+1)), sine eigenvectors
     n = 4001
