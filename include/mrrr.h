@@ -19,6 +19,8 @@
  *    half-open interval (vl, vu].
  *  - d, e, W, Z may be device pointers or host pointers (pageable or
  *    pinned); host buffers are staged through device memory by the call.
+ *    Device buffers must be memory of the device that is current at the
+ *    call (or managed memory); another device's memory is MRRR_ERR_ARG.
  *    The caller owns every buffer.  W must hold k entries and Z n x k
  *    entries, column-major with leading dimension ldz >= n, where
  *    k = iu - il + 1 (MRRR_INDEX), n (MRRR_ALL) or, for MRRR_VALUE, n
@@ -143,8 +145,10 @@ int mrrr_solve_d(int n, const double* d, const double* e, mrrr_range range, doub
  * il[p]..iu[p] when il and iu are non-NULL): nb independent tridiagonals,
  * each solved on its own (Algorithm 1 per matrix), in one sequence of
  * launches over all matrices.  The arrays n, d, e, W, Z, ldz, il, iu,
- * m_out and status are host arrays of length nb; every d[p], e[p], W[p],
- * Z[p] must be a device pointer (n[p] = 1 needs no e[p]).  status[p]
+ * m_out and status are host arrays of length nb; each d[p], e[p], W[p],
+ * Z[p] may be a device pointer or a host pointer, as for mrrr_solve_s (host
+ * inputs are copied to one staging block of device memory before the solve,
+ * host outputs copied back from it after; n[p] = 1 needs no e[p]).  status[p]
  * receives the matrix's own status and m_out[p] (may be NULL) its count.
  * Returns 0 if every matrix succeeded, else the first failing status.
  */
@@ -158,37 +162,47 @@ int mrrr_solve_batch_d(int nb, const int* n, const double* const* d, const doubl
 /*
  * Eigenvectors for given eigenvalues without any device allocation.
  *
- * The paper has no counterpart of this entry point; it exists for callers
- * that cannot allocate device memory at the point of the call -- code running
- * while a CUDA graph is being captured, real-time or embedded hosts that fix
- * their memory at start-up, or libraries whose device memory is owned by
- * another framework's allocator.  It runs the solver's Rayleigh-quotient /
- * twisted-factorization kernel on one fixed scratch array instead of
- * allocated buffers, and calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * The paper has no counterpart of this entry point.  It is for callers that
+ * must not allocate device memory when they call the solver: real-time or
+ * embedded hosts that reserve all their memory at start-up and treat any
+ * later allocation as a failure, and libraries whose device memory belongs
+ * to another framework's allocator, where a cudaMalloc of its own would
+ * bypass that allocator's accounting and limits.  It runs the solver's
+ * Rayleigh-quotient / twisted-factorization kernel on one fixed scratch
+ * array instead of allocated buffers, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
  *
  * Input: T (d[0..n-1], e[0..n-2], binary32, device pointers) and k of its
  * eigenvalues W[0..k-1] = lambda_il .. lambda_{il+k-1} in ascending order
  * (for instance as returned by mrrr_solve_s).  Output: Z (device, n x k,
  * column-major, leading dimension ldz >= n), column t the unit eigenvector of
- * lambda_{il+t}, largest entry positive.  Work: root representation with
- * binary64 internals as in mrrr_solve_s (MRRR_MIXED), each given eigenvalue
- * bracketed by binary64 Sturm counts, then the RQI of Algorithm 1, line 10,
- * on that one representation -- no representation tree, so eigenvalues must
- * be separated relative to each other by more than 1e-5 (the mixed gaptol);
- * within tighter clusters use mrrr_solve_s.  The matrix must not split (no
- * |e_i| <= 2^-24 ||T||_1).
+ * lambda_{il+t}, largest entry positive.  Work: the root representation with
+ * binary64 internals as in mrrr_solve_s (MRRR_MIXED, the same parameter
+ * defaults), each given eigenvalue bracketed by binary64 Sturm counts, the
+ * eigenvalues just below and just above the range bracketed by bisection
+ * (they bound the gaps of the first and last given eigenvalue, as in the
+ * solver), then Rayleigh quotient iteration with twisted factorizations on
+ * that one representation.  There is no representation tree, so the given
+ * eigenvalues must be separated relative to each other by more than 1e-5
+ * (the mixed gaptol); within tighter clusters use mrrr_solve_s.  The matrix
+ * must not split (no |e_i| <= 2^-24 ||T||_1).
  *
- * Limits: n <= MRRR_NOALLOC_MAX_N and k <= MRRR_NOALLOC_MAX_K; larger sizes,
- * host pointers and reducible matrices return MRRR_ERR_ARG (nothing is
- * launched).  The scratch is one file-scope device array of
- * MRRR_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
- * until the process exits.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current, so make
- * that first call before any stream capture begins.  All calls share the
- * array and it keeps the previous call's contents; calls whose work overlaps
- * on the GPU (other streams, other host threads) race and must be serialised
- * by the caller.  The call returns when the results are complete on `stream`.
+ * Errors: sizes beyond the limits below, other invalid sizes, NULL or host
+ * pointers, and device memory of a device other than the current one return
+ * MRRR_ERR_ARG before anything is launched.  A reducible matrix is detected
+ * on the device: the call then returns MRRR_ERR_ARG after its kernels ran,
+ * with Z not written; non-finite input likewise returns MRRR_ERR_NONFINITE.
+ *
+ * Limits: n <= MRRR_NOALLOC_MAX_N and k <= MRRR_NOALLOC_MAX_K.  The scratch
+ * is one file-scope device array of MRRR_NOALLOC_SCRATCH_BYTES bytes that
+ * every GPU loading the library holds until the process exits.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture begins.  All calls share the array and it keeps
+ * the previous call's contents (each call clears what must start at zero);
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  The call reads its status
+ * back and synchronises `stream` before it returns.
  */
 #define MRRR_NOALLOC_MAX_N 1024
 #define MRRR_NOALLOC_MAX_K 1024

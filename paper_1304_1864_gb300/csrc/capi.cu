@@ -6,12 +6,14 @@
 #include <unordered_map>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <type_traits>
 #include <vector>
 
 #include "mrrr.h"
 #include "mrrr_entry.h"
+#include "mrrr_host.h"
 
 namespace {
 
@@ -159,43 +161,11 @@ void rqi_tune_report(unsigned key, int trial, float ms) {
 
 namespace {
 
-bool on_device(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// Paper defaults (Sec. 2, Sec. 3.2, Sec. 4.1); see mrrr.h.
-SolveCfg make_cfg(bool x_single, bool mixed, const mrrr_params* prm) {
-    SolveCfg c;
-    const double eps_s = 5.9604644775390625e-08, eps_d = 1.1102230246251565e-16, eps_dd = 4.930380657631324e-32;
-    c.eps_x = x_single ? eps_s : eps_d;
-    c.eps_y = mixed ? (x_single ? eps_d : eps_dd) : c.eps_x;
-    c.mixed = mixed ? 1 : 0;
-    double gt = mixed ? (x_single ? 1e-5 : 1e-10) : (x_single ? 3e-3 : 1e-3);
-    double xi = mixed ? 4.0 * c.eps_x : 8.0 * c.eps_x;
-    c.krs = 1.0;
-    c.max_rqi = 10;
-    c.seed = 0;
-    c.flags = 0;
-    if (prm) {
-        if (prm->gaptol > 0) gt = prm->gaptol;
-        if (prm->xi > 0) xi = prm->xi;
-        if (prm->krs > 0) c.krs = prm->krs;
-        if (prm->max_rqi > 0) c.max_rqi = prm->max_rqi;
-        c.seed = prm->seed;
-        c.flags = prm->flags;
-    }
-    c.gaptol = gt;
-    c.rtol_class = 1e-2 * gt;
-    c.xi = xi;
-    c.growth_k = 8.0;
-    return c;
-}
+using mrrr::classify_ptr;
+using mrrr::make_cfg;
+using mrrr::PTR_DEVICE;
+using mrrr::PTR_HOST;
+using mrrr::PTR_OTHER_DEVICE;
 
 struct DevBuf {
     void* p = nullptr;
@@ -234,18 +204,22 @@ int solve_one(int n, const X* d, const X* e, mrrr_range range, X vl, X vu, int i
     int dldz = ldz;
     static const X zero1[1] = {X(0)};
     if (n == 1) e = zero1;
-    if (!on_device(d)) {
+    const mrrr::PtrKind kd = classify_ptr(d), ke = n > 1 ? classify_ptr(e) : PTR_HOST;
+    const mrrr::PtrKind kw = classify_ptr(W), kz = classify_ptr(Z);
+    if (kd == PTR_OTHER_DEVICE || ke == PTR_OTHER_DEVICE || kw == PTR_OTHER_DEVICE || kz == PTR_OTHER_DEVICE)
+        return MRRR_ERR_ARG;
+    if (kd == PTR_HOST) {
         if (!bd.alloc(sizeof(X) * n)) return MRRR_ERR_NOMEM;
         if (cudaMemcpyAsync(bd.p, d, sizeof(X) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) return MRRR_ERR_CUDA;
         dd_ = (const X*)bd.p;
     }
-    if (!on_device(e)) {
+    if (ke == PTR_HOST) {
         size_t ne = n > 1 ? (size_t)(n - 1) : 1;
         if (!be.alloc(sizeof(X) * ne)) return MRRR_ERR_NOMEM;
         if (cudaMemcpyAsync(be.p, e, sizeof(X) * ne, cudaMemcpyHostToDevice, st) != cudaSuccess) return MRRR_ERR_CUDA;
         de_ = (const X*)be.p;
     }
-    const bool hostW = !on_device(W), hostZ = !on_device(Z);
+    const bool hostW = kw == PTR_HOST, hostZ = kz == PTR_HOST;
     if (hostW) {
         if (!bw.alloc(sizeof(X) * kmax)) return MRRR_ERR_NOMEM;
         dW = (X*)bw.p;
@@ -295,6 +269,12 @@ int solve_one(int n, const X* d, const X* e, mrrr_range range, X vl, X vu, int i
     return rc;
 }
 
+// Byte offsets of the host-side buffers of a batch inside one staging block
+// of device memory (each 256-byte aligned).
+struct Staged {
+    size_t d = SIZE_MAX, e = SIZE_MAX, W = SIZE_MAX, Z = SIZE_MAX;
+};
+
 template <class X>
 int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const int* il, const int* iu,
                mrrr_mode mode, const mrrr_params* prm, int* m_out, X* const* W, X* const* Z, const int* ldz,
@@ -311,13 +291,20 @@ int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const
     }
     std::vector<MatrixDesc> mats;
     std::vector<int> map;  // mats index -> batch index
+    std::vector<Staged> staged;
     static const X zero1[1] = {X(0)};
     X* dzero = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
+    size_t stage_bytes = 0;
+    auto take = [&](size_t bytes) {
+        size_t off = stage_bytes;
+        stage_bytes += (bytes + 255) / 256 * 256;
+        return off;
+    };
     for (int p = 0; p < nb; ++p) {
         status[p] = MRRR_OK;
         if (m_out) m_out[p] = 0;
-        if (n[p] < 0 || (n[p] > 0 && (ldz[p] < n[p] || !d[p] || !W[p] || !Z[p] || (n[p] > 1 && !e[p])))) {
+        if (n[p] < 0 || (n[p] > 0 && (ldz[p] < n[p] || !d[p] || !W[p] || !Z[p] || (n[p] > 1 && (!e || !e[p]))))) {
             status[p] = MRRR_ERR_ARG;
             continue;
         }
@@ -326,10 +313,25 @@ int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const
             continue;
         }
         if (n[p] == 0) continue;
+        // host buffers are staged through one block of device memory; device
+        // buffers of another device are an argument error
+        const mrrr::PtrKind kd = classify_ptr(d[p]), ke = n[p] > 1 ? classify_ptr(e[p]) : PTR_DEVICE;
+        const mrrr::PtrKind kw = classify_ptr(W[p]), kz = classify_ptr(Z[p]);
+        if (kd == PTR_OTHER_DEVICE || ke == PTR_OTHER_DEVICE || kw == PTR_OTHER_DEVICE || kz == PTR_OTHER_DEVICE) {
+            status[p] = MRRR_ERR_ARG;
+            continue;
+        }
+        const size_t np = (size_t)n[p];
+        const size_t kp = il ? (size_t)(iu[p] - il[p] + 1) : np;
+        Staged sg;
+        if (kd == PTR_HOST) sg.d = take(sizeof(X) * np);
+        if (ke == PTR_HOST) sg.e = take(sizeof(X) * (np - 1));
+        if (kw == PTR_HOST) sg.W = take(sizeof(X) * kp);
+        if (kz == PTR_HOST) sg.Z = take(sizeof(X) * np * kp);
         MatrixDesc M;
         memset(&M, 0, sizeof(M));
         M.d = d[p];
-        M.e = e ? (const void*)e[p] : nullptr;
+        M.e = (e && n[p] > 1) ? (const void*)e[p] : nullptr;
         M.W = W[p];
         M.Z = Z[p];
         M.ldz = ldz[p];
@@ -337,7 +339,34 @@ int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const
         M.range = il ? MRRR_INDEX : MRRR_ALL;
         M.il = il ? il[p] : 1;
         M.iu = il ? iu[p] : n[p];
-        if (n[p] == 1 || !M.e) {
+        mats.push_back(M);
+        map.push_back(p);
+        staged.push_back(sg);
+    }
+    int rc = MRRR_OK;
+    DevBuf stage(st);
+    if (stage_bytes > 0 && !stage.alloc(stage_bytes)) return MRRR_ERR_NOMEM;
+    char* sbase = (char*)stage.p;
+    for (size_t q = 0; q < mats.size(); ++q) {
+        MatrixDesc& M = mats[q];
+        const Staged& sg = staged[q];
+        const size_t np = (size_t)M.n;
+        if (sg.d != SIZE_MAX) {
+            if (cudaMemcpyAsync(sbase + sg.d, M.d, sizeof(X) * np, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return MRRR_ERR_CUDA;
+            M.d = sbase + sg.d;
+        }
+        if (sg.e != SIZE_MAX) {
+            if (cudaMemcpyAsync(sbase + sg.e, M.e, sizeof(X) * (np - 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return MRRR_ERR_CUDA;
+            M.e = sbase + sg.e;
+        }
+        if (sg.W != SIZE_MAX) M.W = sbase + sg.W;
+        if (sg.Z != SIZE_MAX) {
+            M.Z = sbase + sg.Z;
+            M.ldz = M.n;
+        }
+        if (M.n == 1 || !M.e) {
             if (!dzero) {
                 if (!(dzero = (X*)mrrr::dev_alloc(sizeof(X), st))) return MRRR_ERR_NOMEM;
                 if (cudaMemcpyAsync(dzero, zero1, sizeof(X), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -345,10 +374,7 @@ int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const
             }
             M.e = dzero;
         }
-        mats.push_back(M);
-        map.push_back(p);
     }
-    int rc = MRRR_OK;
     if (!mats.empty()) {
         SolveCfg cfg = make_cfg(xs, mode == MRRR_MIXED, prm);
         int max_depth = (prm && prm->max_depth > 0) ? prm->max_depth : 16;
@@ -368,6 +394,23 @@ int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const
                         : sp == mrrr::ST_ERR_NOCONV  ? MRRR_ERR_NOCONV
                                                      : (rc == MRRR_OK || rc == MRRR_ERR_NOCONV ? MRRR_OK : rc);
             if (m_out) m_out[p] = mats[q].kout;
+        }
+        // results of host outputs back from the staging block
+        if (rc == MRRR_OK || rc == MRRR_ERR_NOCONV) {
+            for (int q = 0; q < P; ++q) {
+                const MatrixDesc& M = mats[q];
+                const Staged& sg = staged[q];
+                const int p = map[q];
+                const int k = M.kout;
+                if (k <= 0) continue;
+                if (sg.W != SIZE_MAX &&
+                    cudaMemcpyAsync(W[p], M.W, sizeof(X) * (size_t)k, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    return MRRR_ERR_CUDA;
+                if (sg.Z != SIZE_MAX &&
+                    cudaMemcpy2DAsync(Z[p], sizeof(X) * (size_t)ldz[p], M.Z, sizeof(X) * (size_t)M.n,
+                                      sizeof(X) * (size_t)M.n, k, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    return MRRR_ERR_CUDA;
+            }
         }
     }
     mrrr::dev_free(dzero, st);

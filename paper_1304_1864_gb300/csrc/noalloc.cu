@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "mrrr.h"
+#include "mrrr_host.h"
 #include "mrrr_phases.cuh"
 
 namespace {
@@ -37,8 +38,56 @@ static __device__ __align__(256) unsigned char g_scratch[kBytes];
 
 enum : int { NA_OK = 0, NA_NONFINITE = 1, NA_REDUCIBLE = 2 };
 
-// Kernel 1 (one CTA): scale, check irreducibility, root representation.
-__global__ void k_noalloc_root(unsigned char* base, const float* d, const float* e, int n, SolveCfg cfg) {
+// The status slot (256 bytes) holds the status word and, after it, the
+// brackets of the two eigenvalues just outside the given range in the root
+// representation: [lo, hi] of lambda_{il-1} and of lambda_{il+k} (an absent
+// neighbour has lo = hi = NaN).
+constexpr size_t kOffNbr = kOffStatus + 8;
+static_assert(kOffNbr + 4 * sizeof(double) <= kOffWd, "neighbour brackets must fit in the status slot");
+
+// Bracket of eigenvalue j of the root rep by multisection on the 32 lanes of
+// one warp: each sweep counts at 32 equispaced interior points (count_at,
+// the tuned binary64 Sturm count) and keeps the sub-interval where the count
+// reaches j, down to relative width rtol.  Invariant count(lo) < j <=
+// count(hi); the first point whose count reaches j is the new upper end and
+// the point before it the new lower end, which stays well defined where
+// rounding makes the counts non-monotone.
+__device__ void warp_bracket(const double* rep, int n, int j, double pivmin, double rtol, double lo, double hi,
+                             double* out) {
+    const int q = threadIdx.x & 31;
+    for (int it = 0; it < 64; ++it) {
+        const double tol = fmax(rtol * fmax(fabs(lo), fabs(hi)), 2.0 * pivmin);
+        if (!(tol < hi - lo)) break;
+        const double x = lo + (hi - lo) * (double)(q + 1) / 33.0;
+        const bool inside = x > lo && x < hi;
+        const int c = inside ? count_at<double, true>(rep, rep + 3 * n, n, x, pivmin) : 0;
+        const unsigned reach = __ballot_sync(0xffffffffu, inside && c >= j);
+        const unsigned in = __ballot_sync(0xffffffffu, inside);
+        if (!in) break;  // no representable interior point left
+        const int f = reach ? __ffs(reach) - 1 : 32;
+        // new ends from the lanes' points (points outside the bracket are skipped)
+        double nhi = hi, nlo = lo;
+        for (int k = 0; k < 32; ++k) {
+            const double xk = __shfl_sync(0xffffffffu, x, k);
+            if (!((in >> k) & 1u)) continue;
+            if (k < f) nlo = xk;
+            else if (k == f) nhi = xk;
+        }
+        lo = nlo;
+        hi = nhi;
+    }
+    if (q == 0) {
+        out[0] = lo;
+        out[1] = hi;
+    }
+}
+
+// Kernel 1 (one CTA of 64 threads): scale, check irreducibility, root
+// representation, then (one warp each) the brackets of the eigenvalues just
+// below and just above the given range, which bound the gaps of the first
+// and last given eigenvalue as the outer neighbours do in the solver.
+__global__ void k_noalloc_root(unsigned char* base, const float* d, const float* e, int n, int il, int k,
+                               SolveCfg cfg) {
     MatrixDesc& M = *(MatrixDesc*)(base + kOffMat);
     BlockDesc& B = *(BlockDesc*)(base + kOffBlk);
     int* status = (int*)(base + kOffStatus);
@@ -87,6 +136,8 @@ __global__ void k_noalloc_root(unsigned char* base, const float* d, const float*
         s_bad = bad;
         if (bad == NA_OK) root_bounds<double>(B, wd, we, &s_gl, &s_gu);
     }
+    double* nbr = (double*)(base + kOffNbr);
+    if (threadIdx.x < 4) nbr[threadIdx.x] = NAN;
     __syncthreads();
     if (s_bad != NA_OK) return;
     if (n == 1) {
@@ -103,6 +154,10 @@ __global__ void k_noalloc_root(unsigned char* base, const float* d, const float*
     for (int i = threadIdx.x; i < n; i += blockDim.x) root_move<double>(B, rep, i);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) root_element<double, float>(B, M, rep, rep_lo, i, cfg);
+    __syncthreads();
+    const int w = threadIdx.x >> 5;  // warp 0: lambda_{il-1}, warp 1: lambda_{il+k}
+    const int j = w == 0 ? il - 1 : il + k;
+    if (j >= 1 && j <= n) warp_bracket(rep, n, j, B.pivmin, cfg.rtol_class, B.gl, B.gu, nbr + 2 * w);
 }
 
 // Kernel 2 (one thread per eigenvalue): bracket the given eigenvalue
@@ -140,9 +195,14 @@ __global__ void k_noalloc_rqi(unsigned char* base, const float* W, int il, int k
     int fails = 0;
     verify_endpoint<double>(I, B, 0, &fails);
     verify_endpoint<double>(I, B, 1, &fails);
-    // gaps from the neighbouring given eigenvalues (one side open at the ends)
-    I.gapL = t > 0 ? fmax(lam - ((double)W[t - 1] * M.scale - B.mu) - w, 0.5 * w) : INFINITY;
-    I.gapR = t + 1 < k ? fmax(((double)W[t + 1] * M.scale - B.mu) - lam - w, 0.5 * w) : INFINITY;
+    // gaps from the neighbouring given eigenvalues; at the ends of the range,
+    // from the bracket of the eigenvalue just outside it (none beyond
+    // lambda_1 or lambda_n)
+    const double* nbr = (const double*)(base + kOffNbr);
+    if (t > 0) I.gapL = fmax(lam - ((double)W[t - 1] * M.scale - B.mu) - w, 0.5 * w);
+    else I.gapL = il > 1 ? fmax(lam - nbr[1] - w, 0.5 * w) : INFINITY;
+    if (t + 1 < k) I.gapR = fmax(((double)W[t + 1] * M.scale - B.mu) - lam - w, 0.5 * w);
+    else I.gapR = il + k <= n ? fmax(nbr[2] - lam - w, 0.5 * w) : INFINITY;
     Scratch<double> Wk;
     Wk.a = (double*)(base + kOffWork) + (size_t)t * 2 * kMaxN;
     Wk.b = Wk.a + kMaxN;
@@ -176,15 +236,6 @@ int scratch_address(unsigned char** out) {
     return MRRR_OK;
 }
 
-bool is_device_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 
 extern "C" int mrrr_eigvecs_noalloc_s(int n, const float* d, const float* e, int il, int k, const float* W,
@@ -197,27 +248,19 @@ extern "C" int mrrr_eigvecs_noalloc_s(int n, const float* d, const float* e, int
         cudaGetLastError();
         return MRRR_ERR_CUDA;
     }
-    if (!is_device_ptr(d) || (n > 1 && !is_device_ptr(e)) || !is_device_ptr(W) || !is_device_ptr(Z))
+    // every buffer must be device memory of the current device
+    if (classify_ptr(d) != PTR_DEVICE || (n > 1 && classify_ptr(e) != PTR_DEVICE) || classify_ptr(W) != PTR_DEVICE ||
+        classify_ptr(Z) != PTR_DEVICE)
         return MRRR_ERR_ARG;
     unsigned char* base = nullptr;
     int rc = scratch_address(&base);
     if (rc != MRRR_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    SolveCfg cfg;
-    cfg.eps_x = 5.9604644775390625e-08;
-    cfg.eps_y = 1.1102230246251565e-16;
-    cfg.mixed = 1;
-    cfg.gaptol = 1e-5;
-    cfg.rtol_class = 1e-7;
-    cfg.xi = 4.0 * cfg.eps_x;
-    cfg.krs = 1.0;
-    cfg.growth_k = 8.0;
-    cfg.max_rqi = 10;
-    cfg.seed = 0;
-    cfg.flags = 0;
+    // the defaults of mrrr_solve_s in MRRR_MIXED mode
+    const SolveCfg cfg = make_cfg(true, true, nullptr);
     // the counters of the previous call must not leak into this one
     if (cudaMemsetAsync(base + kOffCnt, 0, sizeof(DevCounters), st) != cudaSuccess) return MRRR_ERR_CUDA;
-    k_noalloc_root<<<1, 64, 0, st>>>(base, d, n > 1 ? e : d, n, cfg);
+    k_noalloc_root<<<1, 64, 0, st>>>(base, d, n > 1 ? e : d, n, il, k, cfg);
     k_noalloc_rqi<<<(k + 63) / 64, 64, 0, st>>>(base, W, il, k, Z, ldz, cfg);
     if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
     int status = 0;

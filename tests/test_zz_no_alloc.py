@@ -1,14 +1,16 @@
 """mrrr_eigvecs_noalloc_s: eigenvectors for given eigenvalues with no device
 allocation.
 
-This entry point is for callers that cannot allocate device memory when they
-call the solver -- for example while a CUDA graph is being captured, in a
-real-time host that fixes its memory at start-up, or inside a library whose
-device memory belongs to another framework's allocator.  Its scratch is one
-fixed device array inside libmrrr.so.  The GPU test checks its eigenvectors
-against those of mrrr_solve_s (the allocating entry point) on two calls in a
-row, with different sizes, so that a call that depended on leftovers of the
-previous one would fail.
+This entry point is for callers that must not allocate device memory when
+they call the solver: real-time or embedded hosts that reserve all their
+memory at start-up, and libraries whose device memory belongs to another
+framework's allocator.  Its scratch is one fixed device array inside
+libmrrr.so.  The GPU test checks its eigenvectors against those of
+mrrr_solve_s (the allocating entry point) on two calls in a row, with
+different sizes, so that a call that depended on leftovers of the previous
+one would fail.  The second call asks for an index range in the middle of
+the spectrum, whose first and last eigenvalues take their gaps from the
+eigenvalues just outside the range.
 
 This file is named so that pytest collects it last.
 """
