@@ -5,14 +5,17 @@ single/double configuration -- 1-2-1 Toeplitz, Wilkinson W_4001 and Clement --
 float32 in/out with binary64 internals, all eigenpairs, the three matrices in
 one mrrr_solve_batch_s call (each solved on its own, Algorithm 1 per matrix,
 in one sequence of launches).  Inputs are resident on the device; L2 is
-flushed (256 MiB write) between timed steps.  Also reported: the same step as
-three sequential and as three concurrent mrrr_solve_s calls, the 4096-matrix
-batched workload, the double-double glued-Wilkinson solve and a bounded
-replay of the serving trace.
+flushed (256 MiB write) between timed steps.  Also reported: plain MRRR
+(binary32 and binary64 inside) on the same matrices with the residual and
+orthogonality of every leg, the step end to end through the C ABI with host
+buffers, the same step as three sequential and as three concurrent
+mrrr_solve_s calls, the 4096-matrix batched workload, the double-double
+glued-Wilkinson solve and a sweep of offered rates through the serving loop.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun every rank solves its own copy of the workload (weak scaling,
-no collective on the data path); rank 0 prints one JSON line.
+--gpus N > 1 outside a distributed launcher starts N ranks through
+torch.distributed.run.  Every rank solves its own copy of the workload (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
 """
 import argparse
 import json
@@ -32,13 +35,19 @@ if ROOT not in sys.path:
 METRIC = "eigenpairs/s (mixed-precision MRRR, all pairs)"
 UNIT = "eigenpairs/s"
 WORKLOAD = "3 x n=4001 tridiagonals (1-2-1, Wilkinson W_4001, Clement), fp32 in/out, fp64 internals, all eigenpairs"
-# FP64 peak of one GB300: 152 SMs x 2 FP64 FMA units x 2 flop x 2070 MHz
-# (matches the 1.25 TFLOP/s nominal figure; a DFMA loop measured 1194 GFLOP/s at 1987 MHz)
+# FP64 peak of one GB300 derived from unit counts and the clock: 152 SMs x 2
+# FP64 FMA per clock per SM x 2 flop x 2070 MHz (the nominal 1.25 TFLOP/s)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-# algorithmic flops per counted qd step (one row of one transform)
-FLOPS_PER_STEP = {"bisect": 4.0, "refine": 4.0, "rqi": 7.5, "shift": 5.0}
-PHASE_COUNTER = {"bisect": "qd_bisect", "refine": "qd_refine", "rqi": "qd_rqi", "shift": "qd_shift"}
-PHASE_KERNEL = {"bisect": "k_bisect", "refine": "k_bisect", "rqi": "k_rqi", "shift": "k_shift"}
+# Algorithmic flops of the Rayleigh quotient iteration (Algorithm 1, line 10;
+# Sec. 2, "Rayleigh quotient iteration"), counted per row of the step's block:
+# one step is the stationary and the progressive transform (3 flops each, the
+# divides not counted) and gamma_k (2 flops) = 8 per row; forming the vector
+# (recurrence, norm, scale) = 3 per row per eigenpair.  In double-double the
+# same operations are counted as binary64 instructions with the multipliers
+# add ~10, mul ~4, div ~17 (FMA-based TwoSum/TwoProd and long division): a
+# step row has 6 adds, 2 muls and 2 divides = 102, a vector row 3 muls and 1
+# add = 22.
+RQI_FLOPS = {"f64": (8.0, 3.0), "dd": (102.0, 22.0)}
 # DRAM bytes (read + write) per k_rqi launch on this workload, the mean over the
 # launches of one `ncu --set full` capture; valid only while the sources that
 # define the kernel hash to the value they had at the capture
@@ -283,16 +292,18 @@ class _Solo:
 
 
 class _Batch:
-    """The C2 step: the three matrices in one mrrr_solve_batch_s call (each
-    matrix solved on its own, Algorithm 1 per matrix, in one sequence of
-    launches over all of them), on the caller's stream."""
+    """One step: the matrices in one mrrr_solve_batch call (each matrix solved
+    on its own, Algorithm 1 per matrix, in one sequence of launches over all
+    of them), on the caller's stream."""
 
-    def __init__(self, m, mats):
-        self.m, self.mats = m, mats
+    def __init__(self, m, mats, mode="mixed"):
+        self.m, self.mats, self.mode = m, mats, mode
+        self.last = None
 
     def run(self, timing=False):
-        out, st, status = self.m.solve_batch(self.mats, mode="mixed", timing=timing, check=False)
+        out, st, status = self.m.solve_batch(self.mats, mode=self.mode, timing=timing, check=False)
         assert all(s == 0 for s in status), status
+        self.last = out
         return [dict(st)]
 
 
@@ -318,6 +329,83 @@ def _time_steps(fn, steps, dev, flush):
 PHASES_L = ("prep", "root", "bisect", "classify", "shift", "refine", "rqi", "finish")
 
 
+def _sum_stats(outs):
+    """Phase times, launches and counters summed over the solves of the timed steps."""
+    acc = {"launches": 0, "rqi_rows": 0, "rqi_iters": 0}
+    for sts in outs:
+        for st in sts:
+            acc["launches"] += sum(st["phase_launches"].values())
+            for k in PHASES_L:
+                acc["ms_" + k] = acc.get("ms_" + k, 0.0) + st["phase_ms"][k]
+                acc["n_" + k] = acc.get("n_" + k, 0) + st["phase_launches"][k]
+            for k in ("qd_bisect", "qd_refine", "qd_rqi", "qd_shift", "rqi_rows", "rqi_iters"):
+                acc[k] = acc.get(k, 0) + st[k]
+    return acc
+
+
+def _rqi_roofline(acc, pairs_rows, arith, peak_measured, traffic=None):
+    """Roofline of k_rqi over the timed steps: algorithmic flops (RQI_FLOPS:
+    per row of each RQI step, plus per row of each eigenpair's vector) over the
+    summed CUDA-event time of its launches (on the streams they run on),
+    against the derived FP64 peak (ALU bound; dd counted in binary64
+    instructions) and against the measured DFMA rate."""
+    per_step, per_vec = RQI_FLOPS[arith]
+    flops = acc["rqi_rows"] * per_step + pairs_rows * per_vec
+    ms = acc["ms_rqi"]
+    launches = max(acc["n_rqi"], 1)
+    achieved = flops / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    phase_ms = {k: acc["ms_" + k] for k in PHASES_L}
+    tot = max(sum(phase_ms.values()), 1e-30)
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+            "kernel": "k_rqi<float, double>" if arith == "f64" else "k_rqi<double, dd>",
+            "launches": acc["n_rqi"], "ms_per_launch": ms / launches, "flops_per_launch": flops / launches,
+            "flop_count": "%g per row per RQI step (rqi_rows = %d) + %g per row per eigenpair (%d rows)" % (
+                per_step, acc["rqi_rows"], per_vec, pairs_rows),
+            "peak_note": "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
+            "peak_measured_gflops": peak_measured,
+            "frac_of_measured": achieved / peak_measured if peak_measured else None,
+            "phase_share": {k: v / tot for k, v in phase_ms.items()}}
+
+
+def _accuracy(pairs):
+    """Largest residual ||T z - w z||_2 / (||T||_1 n eps_x) and orthogonality
+    max |Z^T Z - I| / (n eps_x) over the solved matrices, evaluated on the
+    device in binary64 (products of binary32 data are exact there; for
+    binary64 data the accumulation error, about sqrt(n) eps_d, is far below
+    the n eps_d unit).  pairs: list of (d, e, W, Z) device tensors."""
+    import torch
+    res, orth = 0.0, 0.0
+    for d, e, W, Z in pairs:
+        eps = 2.0 ** -24 if d.dtype == torch.float32 else 2.0 ** -53
+        n = d.shape[0]
+        d64, e64 = d.double(), e.double()
+        Z64, W64 = Z.double(), W.double()
+        TZ = d64[:, None] * Z64
+        TZ[:-1] += e64[:, None] * Z64[1:]
+        TZ[1:] += e64[:, None] * Z64[:-1]
+        R = TZ - Z64 * W64[None, :]
+        absd = d64.abs()
+        rows = absd.clone()
+        rows[:-1] += e64.abs()
+        rows[1:] += e64.abs()
+        tn = float(rows.max())
+        res = max(res, float(R.norm(dim=0).max()) / (tn * n * eps))
+        G = Z64.T @ Z64
+        G.diagonal().sub_(1.0)
+        orth = max(orth, float(G.abs().max()) / (n * eps))
+    return res, orth
+
+
+def _probe_peak(m):
+    try:
+        g, t = m.probe_fp64()
+        return g, t
+    except Exception as ex:  # noqa: BLE001 - reported in the line
+        _log("fp64 probe failed: %s" % ex)
+        return None, None
+
+
 def run_ours(args):
     import torch
     rank, world, local = _dist()
@@ -329,9 +417,11 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     import paper_1304_1864_gb300 as m
     m.lib()
+    peak_meas, peak_ms = _probe_peak(m)
     mats_h = _workload()
     mats = [(torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev)) for d, e in mats_h]
     pairs_per_step = sum(d.shape[0] for d, _ in mats_h)
+    pair_rows = sum(d.shape[0] * d.shape[0] for d, _ in mats_h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     step = _Batch(m, mats)
     for _ in range(args.warmup):
@@ -344,41 +434,18 @@ def run_ours(args):
         ms_total, outs = _time_steps(lambda: step.run(timing=True), args.steps, dev, flush)
         torch.cuda.synchronize(dev)
         _barrier(world)
-    acc = {}
-    launches = 0
-    for sts in outs:
-        for st in sts:
-            launches += sum(st["phase_launches"].values())
-            for k in PHASES_L:
-                acc["ms_" + k] = acc.get("ms_" + k, 0.0) + st["phase_ms"][k]
-                acc["n_" + k] = acc.get("n_" + k, 0) + st["phase_launches"][k]
-            for k in ("qd_bisect", "qd_refine", "qd_rqi", "qd_shift"):
-                acc[k] = acc.get(k, 0) + st[k]
+    acc = _sum_stats(outs)
     last = outs[-1]
     ms_max = _max_over_ranks(ms_total, world, dev)
     value = pairs_per_step * args.steps * world / (ms_max / 1e3)
-    # dominant kernel and its roofline (FP64 ALU bound); every launch is timed
-    # with CUDA events on the stream it runs on
-    phase_ms = {k: acc["ms_" + k] for k in PHASES_L}
-    dom = max(PHASE_COUNTER, key=lambda p: phase_ms.get(p, 0.0))
-    flops = acc[PHASE_COUNTER[dom]] * FLOPS_PER_STEP[dom]
-    launches_dom = acc["n_" + dom]
-    achieved = flops / (phase_ms[dom] / 1e3) / 1e9 if phase_ms[dom] > 0 else 0.0
-    traffic = _rqi_traffic() if PHASE_KERNEL[dom] == "k_rqi" else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-                "traffic_note": ("bytes per launch, mean of the launches of one ncu capture of this kernel on this "
-                                 "workload" if traffic else "kernel changed since the last ncu capture"),
-                "kernel": PHASE_KERNEL[dom],
-                "phase": dom, "launches": launches_dom,
-                "ms_per_launch": phase_ms[dom] / max(launches_dom, 1),
-                "flops_per_launch": flops / max(launches_dom, 1),
-                "peak_note": "of derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (the measured "
-                             "peaks file has no FP64 figure; a DFMA loop measured 1194 GFLOP/s)",
-                "phase_share": {k: v / max(sum(phase_ms.values()), 1e-30) for k, v in phase_ms.items()}}
+    roofline = _rqi_roofline(acc, pair_rows * args.steps, "f64", peak_meas, _rqi_traffic())
+    roofline["traffic_note"] = ("bytes per launch, mean of the launches of one ncu capture of this kernel on this "
+                                "workload" if roofline["traffic"] else "kernel changed since the last ncu capture")
     line = None
     if rank == 0:
         _log("timed steps: %.1f ms" % ms_total)
+        comparison = _compare(m, mats, step, args, dev, flush, value)
+        _log("plain comparison done")
         e2e = _e2e(m, mats_h, args, dev)
         _log("e2e done")
         cb = cpu_baseline(mats_h) if (world == 1 and not args.no_cpu_baseline) else None
@@ -389,27 +456,62 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "mode": "mixed single/double (fp32 io, fp64 internals)",
                            "solves": "the 3 matrices in one mrrr_solve_batch_s call: each matrix solved on its "
                                      "own (Algorithm 1 per matrix) in one sequence of launches over all of them",
-                           "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replica per GPU"},
-                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
+                           "l2": "flushed (256 MiB write) between timed steps",
+                           "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": acc["launches"],
                 "clocks": clk.summary(),
+                "fp64_probe": {"gflops": peak_meas, "ms": peak_ms,
+                               "what": "mrrr_probe_fp64_fma: 8 warps per SM, 8 independent DFMA chains per thread"},
+                "comparison": comparison,
                 "tree": {nm: last[0][key] for nm, key in
                          (("d_max", "d_max"), ("clusters", "nclusters"), ("largest_cluster", "largest_cluster"),
                           ("reps_failed", "reps_failed"), ("rqi_iters", "rqi_iters"), ("fallbacks", "fallbacks"))}}
         line["variants"] = _variants(m, mats, args, dev, flush)
         if not args.no_extras:
-            for key, fn in (("c4_batched", lambda: _c4(m, dev, flush)),
-                            ("c3_dd", lambda: _c3(m, dev, flush)),
-                            ("serve", lambda: _serve(m, dev, args.serve_requests))):
+            for key, fn in (("c4_batched", lambda: _c4(m, dev, flush, args, peak_meas)),
+                            ("c3_dd", lambda: _c3(m, dev, flush, args, peak_meas)),
+                            ("serve", lambda: _serve(m, dev, args))):
                 t0 = time.perf_counter()
                 line[key] = fn()
                 _log("%s: %.1f s" % (key, time.perf_counter() - t0))
-        if args.plain:
-            line["plain"] = _plain(m, mats, args, dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _compare(m, mats, step, args, dev, flush, value):
+    """The metric's comparison: mixed precision against plain MRRR on the same
+    three matrices -- plain binary32 (y = x, the same fp32 input) and the plain
+    FP64-internal solver (y = x = binary64, the matrices given as fp64) --
+    each as one batched call, timed like the headline step; then residual and
+    orthogonality of each result in units of n eps of its own I/O precision."""
+    import torch
+    k = max(3, min(args.steps, 20))
+    pairs = sum(d.shape[0] for d, _ in mats)
+    res = {}
+    legs = (("mixed_fp32_fp64", step, mats),
+            ("plain_fp32", _Batch(m, mats, "plain"), mats),
+            ("plain_fp64", _Batch(m, [(d.double(), e.double()) for d, e in mats], "plain"),
+             [(d.double(), e.double()) for d, e in mats]))
+    for label, st, mm in legs:
+        if label != "mixed_fp32_fp64":
+            for _ in range(2):
+                st.run()
+            torch.cuda.synchronize(dev)
+            ms, _ = _time_steps(st.run, k, dev, flush)
+            v = pairs * k / (ms / 1e3)
+        else:
+            v = value
+            st.run()
+        torch.cuda.synchronize(dev)
+        r, o = _accuracy([(d, e, W, Z) for (d, e), (W, Z) in zip(mm, st.last)])
+        res[label] = {"value": v, "unit": UNIT, "residual_neps": r, "orthogonality_neps": o}
+    res["note"] = ("residual ||Tz - wz||_2 / (||T||_1 n eps_x) and orthogonality max|Z^T Z - I| / (n eps_x), "
+                   "worst over the three matrices, eps_x of each leg's I/O precision; binary64 evaluation on the "
+                   "device")
+    return res
 
 
 def _variants(m, mats, args, dev, flush):
@@ -418,6 +520,7 @@ def _variants(m, mats, args, dev, flush):
     import torch
     pairs = sum(d.shape[0] for d, _ in mats)
     res = {}
+    k = max(3, min(args.steps, 20))
 
     def seq():
         for d, e in mats:
@@ -428,41 +531,40 @@ def _variants(m, mats, args, dev, flush):
     for label, fn in (("sequential_solves", seq), ("concurrent_solves", solo.run)):
         fn()
         torch.cuda.synchronize(dev)
-        ms, _ = _time_steps(fn, args.steps, dev, flush)
-        res[label] = {"value": pairs * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps}
+        ms, _ = _time_steps(fn, k, dev, flush)
+        res[label] = {"value": pairs * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k}
     return res
 
 
-def _c4(m, dev, flush):
+def _c4(m, dev, flush, args, peak_meas):
     """Batched workload: 4096 tridiagonals, n log-uniform in [32, 2048], types
     {U(-1,1), 1-2-1, Wilkinson, glued W_21 (coupling 1e-8)}, fp32 in, fp64
-    internals, all eigenpairs, one mrrr_solve_batch_s call; one warm-up call
-    and one timed call."""
+    internals, all eigenpairs, one mrrr_solve_batch_s call per step."""
     import torch
     from paper_1304_1864_gb300 import inputs
     batch = inputs.workload_c4(count=4096, seed=4)
     mats = [(torch.tensor(d, dtype=torch.float32, device=dev), torch.tensor(e, dtype=torch.float32, device=dev))
             for _, d, e in batch]
     pairs = sum(d.size for _, d, _ in batch)
-
-    def step():
-        out, st, status = m.solve_batch(mats, mode="mixed")
-        assert all(s == 0 for s in status)
-        return st
-
-    step()
+    pair_rows = sum(d.size * d.size for _, d, _ in batch)
+    step = _Batch(m, mats)
+    step.run()
     torch.cuda.synchronize(dev)
-    ms, sts = _time_steps(step, 1, dev, flush)
-    st = sts[0]
-    return {"value": pairs / (ms / 1e3), "unit": UNIT, "ms": ms, "matrices": len(batch), "eigenpairs": pairs,
-            "d_max": st["d_max"], "clusters": st["nclusters"], "fallbacks": st["fallbacks"],
+    k = args.extra_steps
+    ms, sts = _time_steps(lambda: step.run(timing=True), k, dev, flush)
+    acc = _sum_stats(sts)
+    st = sts[-1][0]
+    return {"value": pairs * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+            "matrices": len(batch), "eigenpairs": pairs, "d_max": st["d_max"], "clusters": st["nclusters"],
+            "reps_failed": st["reps_failed"], "fallbacks": st["fallbacks"],
+            "roofline": _rqi_roofline(acc, pair_rows * k, "f64", peak_meas),
             "workload": "4096 tridiagonals, n log-uniform [32, 2048], seed 4, types uniform/1-2-1/Wilkinson/"
-                        "glued W_21, fp32 in, fp64 internals, all pairs, one batched call"}
+                        "glued W_21, fp32 in, fp64 internals, all pairs, one batched call per step"}
 
 
-def _c3(m, dev, flush):
+def _c3(m, dev, flush, args, peak_meas):
     """Glued Wilkinson, 40 x W_201 with couplings 1e-8 (n = 8040), fp64 in,
-    double-double internals, all eigenpairs; one warm-up and one timed solve."""
+    double-double internals, all eigenpairs, one mrrr_solve_d per step."""
     import torch
     from paper_1304_1864_gb300 import inputs
     (d, e), = inputs.workload_c3()
@@ -470,26 +572,26 @@ def _c3(m, dev, flush):
     ee = torch.tensor(e, dtype=torch.float64, device=dev)
     m.solve(dd, ee, mode="mixed")
     torch.cuda.synchronize(dev)
-    ms, sts = _time_steps(lambda: m.solve(dd, ee, mode="mixed")[2], 1, dev, flush)
-    st = sts[0]
-    return {"value": d.size / (ms / 1e3), "unit": UNIT, "ms": ms, "n": int(d.size), "d_max": st["d_max"],
-            "clusters": st["nclusters"], "largest_cluster": st["largest_cluster"],
+    k = args.extra_steps
+    ms, sts = _time_steps(lambda: [m.solve(dd, ee, mode="mixed", timing=True)[2]], k, dev, flush)
+    acc = _sum_stats(sts)
+    st = sts[-1][0]
+    n = int(d.size)
+    return {"value": n * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k, "n": n,
+            "d_max": st["d_max"], "clusters": st["nclusters"], "largest_cluster": st["largest_cluster"],
+            "reps_failed": st["reps_failed"], "roofline": _rqi_roofline(acc, n * n * k, "dd", peak_meas),
             "workload": "glued Wilkinson 40 x W_201, couplings 1e-8, n=8040, fp64 in, double-double internals"}
 
 
-def _serve(m, dev, count):
-    """Serving loop: the first `count` requests of the seeded Poisson trace
-    (2000 requests/s, n log-uniform [64, 16384], half fp32 in with fp64
-    internals, half fp64 in with double-double internals, half all pairs, half
-    a random contiguous 10% index range), submitted at their arrival times
-    (host inputs, device outputs) to one server; latency is submit to
+def _serve_run(m, dev, trace):
+    """Submit the requests of `trace` at their arrival times (host inputs,
+    device outputs) to one server and wait for all; latency is submit to
     completion."""
     import torch
     from paper_1304_1864_gb300 import inputs
-    trace = inputs.serving_trace(rate=2000.0, seconds=1.0, seed=5)[:count]
     reqs = []
     for r in trace:
-        d, e = inputs.make(r["kind"], r["n"], seed=int(r["t"] * 1e6) % (2**31))
+        d, e = inputs.make(r["kind"], r["n"], seed=r["seed"])
         n = d.size
         if r["il"] == 1 and r["iu"] == r["n"]:
             il, iu = 0, 0
@@ -524,62 +626,71 @@ def _serve(m, dev, count):
         srv.close()
     return {"requests": len(reqs), "failed": bad, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "max_ms": st["max_ms"], "eigenpairs": st["eigenpairs"], "batches": st["batches"],
-            "value": st["eigenpairs"] / max(st["busy_s"], 1e-9), "unit": UNIT, "wall_s": wall,
-            "offered": "Poisson 2000 requests/s (trace seed 5), first %d requests replayed at their arrival times; "
-                       "n log-uniform [64, 16384]; half fp32->fp64, half fp64->double-double; half all pairs, "
-                       "half 10%% index ranges; 3 workers, budget = half the free HBM" % len(reqs)}
+            "value": st["eigenpairs"] / max(st["busy_s"], 1e-9), "unit": UNIT, "wall_s": wall}
 
 
-def _plain(m, mats, args, dev):
-    """Plain MRRR (working precision = I/O precision: fp32) and the plain
-    FP64 solver run on the same fp32 data as fp64 input, for comparison."""
-    import torch
-    res = {}
-    for label, mm, mode in (("plain_fp32", mats, "plain"),
-                            ("plain_fp64", [(d.double(), e.double()) for d, e in mats], "plain")):
-        for _ in range(2):
-            m.solve_batch(mm, mode=mode)
-        torch.cuda.synchronize(dev)
-        t = 0.0
-        for _ in range(args.steps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            m.solve_batch(mm, mode=mode)
-            b.record()
-            b.synchronize()
-            t += a.elapsed_time(b)
-        res[label] = {"value": sum(d.shape[0] for d, _ in mm) * args.steps / (t / 1e3), "unit": UNIT}
-    return res
+def _serve(m, dev, args):
+    """Serving loop (continuous batching) on the request mix of the serving
+    trace -- n log-uniform [64, 16384], half fp32 in with fp64 internals and
+    half fp64 in with double-double internals, half all pairs and half a
+    random contiguous 10% index range -- at a sweep of Poisson arrival rates
+    up to and past the server's capacity, each for a bounded window; then
+    the first requests of the 2000 requests/s trace as the overload point."""
+    from paper_1304_1864_gb300 import inputs
+    sweep = []
+    for rate in args.serve_rates:
+        trace = inputs.serving_trace(rate=rate, seconds=args.serve_seconds, seed=5)
+        r = _serve_run(m, dev, trace)
+        r["offered_req_per_s"] = rate
+        r["window_s"] = args.serve_seconds
+        sweep.append(r)
+        _log("serve %.1f req/s: %d requests, p50 %.0f ms, p99 %.0f ms" % (rate, r["requests"], r["p50_ms"],
+                                                                            r["p99_ms"]))
+    over = _serve_run(m, dev, inputs.serving_trace(rate=2000.0, seconds=1.0, seed=5)[:args.serve_requests])
+    over["offered"] = ("Poisson 2000 requests/s (trace seed 5), first %d requests replayed at their arrival "
+                       "times" % args.serve_requests)
+    bounded = [r["offered_req_per_s"] for r in sweep if r["failed"] == 0 and r["p99_ms"] <= 4 * max(
+        sweep[0]["p99_ms"], 1.0)]
+    return {"sweep": sweep, "overload_2000_req_s": over,
+            "p99_bounded_up_to_req_s": max(bounded) if bounded else None,
+            "mix": "n log-uniform [64, 16384]; half fp32->fp64, half fp64->double-double; half all pairs, half "
+                   "10% index ranges; host inputs, device outputs; 3 workers, budget = half the free HBM",
+            "bounded_rule": "p99 within 4x of the p99 at the lowest offered rate"}
 
 
 def _e2e(m, mats_h, args, dev):
-    """The C2 step end to end through the public API, as the headline step
-    (one mrrr_solve_batch_s call through the binding's solve_batch): each
-    step copies the inputs from pinned host memory to the device, solves,
-    and copies W and Z back to pinned host memory, all inside the timed
-    region (wall clock, the stream synchronised at the end of every step)."""
+    """The C2 step end to end through the C ABI with host buffers: one
+    mrrr_solve_batch_s call given pinned host pointers for d, e, W and Z (ldz
+    = n); the library copies the inputs to the device, solves, and copies W
+    and Z back before it returns, all inside the timed region (wall clock)."""
+    import ctypes
     import torch
-    pin_in = [(torch.from_numpy(d).pin_memory(), torch.from_numpy(e).pin_memory()) for d, e in mats_h]
-    dev_in = [(torch.empty(d.shape, dtype=d.dtype, device=dev), torch.empty(e.shape, dtype=e.dtype, device=dev))
-              for d, e in pin_in]
-    pin_out = []
-    stream = torch.cuda.current_stream(dev)
+    nb = len(mats_h)
+    n = [d.size for d, _ in mats_h]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    dh = [pin(d) for d, _ in mats_h]
+    eh = [pin(e) for _, e in mats_h]
+    Wh = [torch.empty(k, dtype=torch.float32).pin_memory() for k in n]
+    Zh = [torch.empty((k, k), dtype=torch.float32).pin_memory() for k in n]
+    vp = ctypes.c_void_p
+
+    def arr(t, xs):
+        return ctypes.cast((t * nb)(*xs), vp)
+
+    a_n = arr(ctypes.c_int, n)
+    a_d = arr(vp, [t.data_ptr() for t in dh])
+    a_e = arr(vp, [t.data_ptr() for t in eh])
+    a_w = arr(vp, [t.data_ptr() for t in Wh])
+    a_z = arr(vp, [t.data_ptr() for t in Zh])
+    a_ld = arr(ctypes.c_int, n)
+    status = (ctypes.c_int * nb)()
+    mout = (ctypes.c_int * nb)()
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
 
     def step():
-        for (dh, eh), (dd, ed) in zip(pin_in, dev_in):
-            dd.copy_(dh, non_blocking=True)
-            ed.copy_(eh, non_blocking=True)
-        out, st, status = m.solve_batch(dev_in, mode="mixed", check=False)
-        assert all(s == 0 for s in status), status
-        if not pin_out:
-            for W, Z in out:
-                pin_out.append((torch.empty(W.shape, dtype=W.dtype).pin_memory(),
-                                torch.empty(Z.T.shape, dtype=Z.dtype).pin_memory()))
-        for (W, Z), (Wh, Zh) in zip(out, pin_out):
-            Wh.copy_(W, non_blocking=True)
-            Zh.copy_(Z.T, non_blocking=True)
-        stream.synchronize()
+        rc = m.mrrr_solve_batch_s(nb, a_n, a_d, a_e, None, None, m.MRRR_MIXED, None, ctypes.cast(mout, vp), a_w,
+                                  a_z, a_ld, ctypes.cast(status, vp), stream)
+        assert rc == 0, rc
 
     for _ in range(max(1, args.warmup)):
         step()
@@ -587,12 +698,24 @@ def _e2e(m, mats_h, args, dev):
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
-    pairs = sum(d.size for d, _ in mats_h)
+    pairs = sum(n)
     h2d = sum(4 * (d.size + e.size) for d, e in mats_h)
-    d2h = sum(4 * (d.size + d.size * d.size) for d, _ in mats_h)
+    d2h = sum(4 * (k + k * k) for k in n)
     return {"value": pairs * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "api": "mrrr_solve_batch_s through the binding's solve_batch; inputs copied from pinned host memory and "
-                   "W, Z copied back to pinned host memory inside the timed region"}
+            "api": "mrrr_solve_batch_s with pinned host buffers for d, e, W and Z: the library stages them "
+                   "through device memory inside the call; wall clock per call"}
+
+
+def _spawn(args):
+    """--gpus N outside a distributed launcher: start N ranks on this node
+    through torch.distributed.run (one process per GPU) and return its status."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(args.gpus),
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
 
 
 def main():
@@ -601,11 +724,20 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plain", action="store_true", help="also time the plain (y = x) solvers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, C3, C4 and serving measurements")
-    ap.add_argument("--serve-requests", type=int, default=200, help="requests replayed from the serving trace")
+    ap.add_argument("--extra-steps", type=int, default=10, help="timed steps of the C3 and C4 legs")
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[2.0, 5.0, 10.0, 20.0],
+                    help="offered Poisson rates (requests/s) of the serving sweep")
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="arrival window of each sweep point")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests replayed from the 2000/s trace")
     args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if "WORLD_SIZE" in os.environ and world != args.gpus:
+        sys.stderr.write("bench.py: --gpus %d but WORLD_SIZE=%d\n" % (args.gpus, world))
+        return 2
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return _spawn(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -96,6 +96,8 @@ typedef struct {
     int timed;            /* 1 if phase_ms / phase_launches were measured (MRRR_FLAG_TIMING) */
     int phase_launches[MRRR_NPHASES]; /* kernel launches per phase */
     double phase_ms[MRRR_NPHASES];    /* device time per phase (CUDA events on the solve's stream) */
+    long long rqi_rows;   /* sum over all RQI steps of the order n of the step's block: each step is one
+                             twisted factorization and solve of n rows (Sec. 2) */
 } mrrr_stats;
 
 /* Tuning parameters; a zero field selects the default given in brackets. */

@@ -29,7 +29,7 @@ class MrrrStats(ctypes.Structure):
                 ("qd_shift", ctypes.c_longlong), ("qd_low", ctypes.c_longlong), ("verify_fail", ctypes.c_int),
                 ("reps_relaxed", ctypes.c_int), ("rqi_warps_per_sm", ctypes.c_int),
                 ("timed", ctypes.c_int), ("phase_launches", ctypes.c_int * NPHASES),
-                ("phase_ms", ctypes.c_double * NPHASES)]
+                ("phase_ms", ctypes.c_double * NPHASES), ("rqi_rows", ctypes.c_longlong)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("phase_launches", "phase_ms")}
@@ -109,6 +109,9 @@ def lib():
         for name in ("mrrr_serve_open", "mrrr_serve_submit", "mrrr_serve_poll", "mrrr_serve_stats_get",
                      "mrrr_serve_close"):
             getattr(L, name).restype = ctypes.c_int
+        L.mrrr_probe_fp64_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), vp]
+        L.mrrr_probe_fp64_fma.restype = ctypes.c_int
         L.mrrr_strerror.argtypes = [ctypes.c_int]
         L.mrrr_strerror.restype = ctypes.c_char_p
         L.mrrr_version.argtypes = []
@@ -164,6 +167,21 @@ def mrrr_serve_stats_get(server, out):
 
 def mrrr_serve_close(server):
     return lib().mrrr_serve_close(server)
+
+
+def mrrr_probe_fp64_fma(iters, gflops, ms, stream):
+    return lib().mrrr_probe_fp64_fma(iters, gflops, ms, stream)
+
+
+def probe_fp64(iters=0, stream=None):
+    """Measured binary64 FMA throughput of the current device:
+    (GFLOP/s, milliseconds of the timed launch)."""
+    g = ctypes.c_double(0.0)
+    t = ctypes.c_double(0.0)
+    rc = mrrr_probe_fp64_fma(iters, ctypes.byref(g), ctypes.byref(t), _stream_handle(stream, True))
+    if rc != MRRR_OK:
+        raise MrrrError(rc, "mrrr_probe_fp64_fma")
+    return g.value, t.value
 
 
 def mrrr_strerror(code):

@@ -944,6 +944,7 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
             I.rqi_done = done0 + iters;
             I.rhint = r_hint;
             MRRR_ATOMIC_ADD(&C->rqi_iters, iters);
+            MRRR_ATOMIC_ADD(&C->rqi_rows, (unsigned long long)iters * (unsigned long long)n);
             MRRR_ATOMIC_ADD(&C->qd_rqi, steps);
             if (steps_low) MRRR_ATOMIC_ADD(&C->qd_steps_low, steps_low);
             return false;
@@ -989,6 +990,7 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
         }
     }
     MRRR_ATOMIC_ADD(&C->rqi_iters, iters);
+    MRRR_ATOMIC_ADD(&C->rqi_rows, (unsigned long long)iters * (unsigned long long)n);
     MRRR_ATOMIC_ADD(&C->qd_rqi, steps);
     if (steps_low) MRRR_ATOMIC_ADD(&C->qd_steps_low, steps_low);
     // eigenvalue of T: (lambda + sigma) / scale

@@ -1147,6 +1147,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         stats->verify_fail = C.verify_fail;
         stats->reps_relaxed = C.reps_relaxed;
         stats->rqi_warps_per_sm = rqi_wps;
+        stats->rqi_rows = (long long)C.rqi_rows;
         tl.collect(stats);
     }
     if (arena.failed) return MRRR_ERR_NOMEM;

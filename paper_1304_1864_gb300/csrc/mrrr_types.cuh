@@ -105,6 +105,7 @@ struct DevCounters {
     unsigned long long qd_rqi;     // ... in the Rayleigh quotient iterations (incl. fallbacks)
     unsigned long long qd_shift;   // ... in building child representations
     unsigned long long qd_steps_low;
+    unsigned long long rqi_rows;   // sum over RQI steps of the block order n
     unsigned long long pool_need;  // pool elements requested at the current level
     int nsingle;        // singletons appended to the singleton list
     int ncluster;       // clusters appended at the current level

@@ -51,6 +51,36 @@ def check_eigvals(d, e, W, prec, mode, idx=None, il=1):
     return errs.max() / max(bound, 1e-300)
 
 
+_ORACLE_CACHE = {}
+
+
+def oracle_all(name, d, e):
+    """All eigenvalues (hi + lo of the binary128 bisection) of the named test
+    matrix, computed once per test session (one parallel oracle sweep)."""
+    if name not in _ORACLE_CACHE:
+        hi, lo = oracle.eigvals(d, e)
+        _ORACLE_CACHE[name] = (hi, lo)
+    return _ORACLE_CACHE[name]
+
+
+def check_eigvals_all(d, e, W, prec, mode, lam, il=1):
+    """Every entry W[k] against the oracle eigenvalue il + k (lam = hi + lo of
+    the full oracle spectrum, as two arrays), element by element, within
+    2 n eps_x ||T||_1."""
+    n = d.size
+    W = as_np(W).astype(np.float64)
+    hi, lo = lam
+    ref_hi = hi[il - 1:il - 1 + W.size]
+    ref_lo = lo[il - 1:il - 1 + W.size]
+    # the rounding of these two subtractions is far below the bound
+    err = np.abs((W - ref_hi) - ref_lo)
+    bound = TOL[mode]["eig"] * n * EPS[prec] * metrics.tnorm1(d, e)
+    bad = np.nonzero(~(err <= bound))[0]
+    assert bad.size == 0, "%d eigenvalues off by more than %.3g (worst %.3g at %d)" % (
+        bad.size, bound, err.max(), int(np.argmax(err)))
+    return float(err.max() / bound)
+
+
 def check_res_orth(d, e, W, Z, prec, mode):
     """Residual ||T z - w z||_2 / (||T||_1 n eps) and orthogonality
     max |Z^T Z - I| / (n eps), both with exact accumulation (oracle.metrics)."""

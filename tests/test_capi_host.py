@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI (no GPU needed): the library builds and
-exports every entry point declared in include/mrrr.h, the statistics struct
+exports every entry point declared in include/*.h, the statistics struct
 of the binding matches the header, and invalid arguments are rejected before
 any device work."""
 import ctypes
@@ -16,15 +16,20 @@ HEADER = os.path.join(ROOT, "include", "mrrr.h")
 
 
 def _declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mrrr_\w+)\s*\(", src)))
+    names = set()
+    inc = os.path.dirname(HEADER)
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(mrrr_\w+)\s*\(", src))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol():
     L = m.lib()
     names = _declared_functions()
-    assert {"mrrr_solve_s", "mrrr_solve_d", "mrrr_solve_batch_s", "mrrr_solve_batch_d", "mrrr_strerror"} <= set(names)
+    assert {"mrrr_solve_s", "mrrr_solve_d", "mrrr_solve_batch_s", "mrrr_solve_batch_d", "mrrr_strerror",
+            "mrrr_probe_fp64_fma"} <= set(names)
     for name in names:
         assert hasattr(L, name), "libmrrr.so does not export " + name
 
