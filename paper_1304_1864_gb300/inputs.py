@@ -3,10 +3,13 @@
 This module holds no arithmetic of the eigensolver: it only draws or writes
 down the entries of the test tridiagonals, and is shared by the tests, the
 benchmark and the oracle checks.  The matrix types are the ones the paper
-tests with (Sec. 5: uniform eigenvalue distribution, 1-2-1, Clement,
-Wilkinson, Hermite, and glued Wilkinson matrices); the paper defers their
-definitions to a test-matrix collection that is not reproduced here, so each
-generator states the textbook definition it uses.
+tests with (Sec. 5: uniform and geometric eigenvalue distributions, 1-2-1,
+Clement, Wilkinson and Hermite matrices; glued Wilkinson matrices for tight
+clusters); the paper defers their definitions to a test-matrix collection
+that is not reproduced here, so each generator states the textbook
+definition it uses.  The two eigenvalue-distribution types are built from a
+prescribed spectrum by Lanczos (``from_spectrum``), which is a generator
+step, not part of the eigensolver.
 
 All generators return float64 arrays (d of length n, e of length n-1); a
 caller that wants single-precision input casts them.
@@ -67,12 +70,76 @@ def glued_wilkinson(copies: int, block: int = 201, coupling: float = 1e-8):
     return d, e
 
 
+def from_spectrum(lam, seed: int = 0):
+    """A symmetric tridiagonal whose eigenvalues are ``lam``: the Lanczos
+    tridiagonalisation of diag(lam) from a seeded random unit start vector
+    (numpy PCG64 ``default_rng(seed)``, standard normal entries), in binary64
+    with full reorthogonalisation against every previous Lanczos vector,
+    applied twice per step.  In exact arithmetic T has exactly the spectrum
+    ``lam``; in binary64 each eigenvalue moves by O(eps ||lam||), and the
+    tests take T's eigenvalues from the oracle, never from ``lam``.  Costs
+    about 2 n^3 flops (a few seconds at n = 2500)."""
+    lam = np.asarray(lam, np.float64)
+    n = lam.size
+    rng = np.random.default_rng(seed)
+    Q = np.zeros((n, n))  # row j = Lanczos vector q_j
+    q = rng.standard_normal(n)
+    Q[0] = q / np.linalg.norm(q)
+    d = np.zeros(n)
+    e = np.zeros(max(n - 1, 0))
+    for j in range(n):
+        w = lam * Q[j]
+        d[j] = Q[j] @ w
+        if j == n - 1:
+            break
+        w -= d[j] * Q[j]
+        if j > 0:
+            w -= e[j - 1] * Q[j - 1]
+        for _ in range(2):
+            w -= Q[:j + 1].T @ (Q[:j + 1] @ w)
+        b = np.linalg.norm(w)
+        e[j] = b
+        if b == 0.0:  # invariant subspace found: restart from a fresh direction
+            w = rng.standard_normal(n)
+            for _ in range(2):
+                w -= Q[:j + 1].T @ (Q[:j + 1] @ w)
+            b = np.linalg.norm(w)
+        Q[j + 1] = w / b
+    return d, e
+
+
+def uniform_spectrum(n: int, seed: int = 0, eps: float = 2.0 ** -53):
+    """Eigenvalues evenly spaced in [eps, 1]: lambda_i = eps + (i - 1)(1 - eps)
+    / (n - 1) (the "uniform eigenvalue distribution" type of Sec. 5; the
+    paper defers the definition to its test-matrix collection, this is the
+    arithmetic mode of LAPACK's test-matrix generator with condition 1/eps),
+    as a tridiagonal by ``from_spectrum``."""
+    i = np.arange(n, dtype=np.float64)
+    lam = eps + i * (1.0 - eps) / max(n - 1, 1)
+    return from_spectrum(lam, seed)
+
+
+def geometric_spectrum(n: int, seed: int = 0, eps: float = 2.0 ** -53):
+    """Eigenvalues geometrically spaced from eps to 1: lambda_i =
+    eps^((n - i) / (n - 1)) (the "geometric eigenvalue distribution" type of
+    Sec. 5, the geometric mode of LAPACK's test-matrix generator with
+    condition 1/eps), as a tridiagonal by ``from_spectrum``."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    lam = eps ** ((n - i) / max(n - 1, 1))
+    return from_spectrum(lam, seed)
+
+
 def make(kind: str, n: int, seed: int = 0):
-    """Dispatch by type name: 'uniform', '121', 'wilkinson', 'clement',
-    'hermite', 'glued' (glued copies of W_21, n rounded down to a multiple
-    of 21)."""
+    """Dispatch by type name: 'uniform' (entries U(-1, 1)), '121',
+    'wilkinson', 'clement', 'hermite', 'glued' (glued copies of W_21, n
+    rounded down to a multiple of 21), 'uniform_spectrum' and
+    'geometric_spectrum' (the paper's two eigenvalue-distribution types)."""
     if kind == "uniform":
         return uniform_random(n, seed)
+    if kind == "uniform_spectrum":
+        return uniform_spectrum(n, seed)
+    if kind == "geometric_spectrum":
+        return geometric_spectrum(n, seed)
     if kind == "121":
         return one_two_one(n)
     if kind == "wilkinson":

@@ -81,9 +81,10 @@ def check_eigvals_all(d, e, W, prec, mode, lam, il=1):
     return float(err.max() / bound)
 
 
-def check_res_orth(d, e, W, Z, prec, mode):
+def measure_res_orth(d, e, W, Z, prec):
     """Residual ||T z - w z||_2 / (||T||_1 n eps) and orthogonality
-    max |Z^T Z - I| / (n eps), both with exact accumulation (oracle.metrics)."""
+    max |Z^T Z - I| / (n eps), both with exact accumulation (oracle.metrics),
+    without a verdict."""
     n = d.size
     W = as_np(W).astype(np.float64)
     Z = as_np(Z)
@@ -94,7 +95,12 @@ def check_res_orth(d, e, W, Z, prec, mode):
     r2, _ = metrics.residuals(d, e, W, Z)
     res = float(r2.max() / (tn * ne)) if tn > 0 else float(r2.max())
     off, dia = metrics.ortho(Z, target=ne)
-    orth = max(off, dia) / ne
+    return res, max(off, dia) / ne
+
+
+def check_res_orth(d, e, W, Z, prec, mode):
+    """measure_res_orth, asserted against the targets of the mode (TOL)."""
+    res, orth = measure_res_orth(d, e, W, Z, prec)
     assert res <= TOL[mode]["res"], "residual %.3g n eps ||T|| > %.3g" % (res, TOL[mode]["res"])
     assert orth <= TOL[mode]["orth"], "orthogonality %.3g n eps > %.3g" % (orth, TOL[mode]["orth"])
     return res, orth

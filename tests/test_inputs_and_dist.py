@@ -84,3 +84,22 @@ def test_max_over_ranks_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert sorted(out) == [(0, 20.0), (1, 20.0)]
+
+
+@pytest.mark.parametrize("kind", ["uniform_spectrum", "geometric_spectrum"])
+def test_spectrum_generators_reach_their_spectrum(kind):
+    # the Lanczos tridiagonal of diag(lambda) has the prescribed eigenvalues up
+    # to binary64 rounding (LAPACK's tridiagonal eigenvalues as the check)
+    sl = pytest.importorskip("scipy.linalg")
+    n = 300
+    d, e = inputs.make(kind, n, seed=3)
+    lam = sl.eigvalsh_tridiagonal(d, e)
+    i = np.arange(n)
+    eps = 2.0 ** -53
+    want = eps + i * (1 - eps) / (n - 1) if kind == "uniform_spectrum" else eps ** ((n - 1 - i) / (n - 1))
+    assert np.max(np.abs(lam - want)) <= 64 * n * eps
+    # seeded: the same matrix every time, another one for another seed
+    d2, e2 = inputs.make(kind, n, seed=3)
+    assert np.array_equal(d, d2) and np.array_equal(e, e2)
+    d3, _ = inputs.make(kind, n, seed=4)
+    assert not np.array_equal(d, d3)
