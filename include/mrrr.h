@@ -162,6 +162,29 @@ int mrrr_solve_batch_d(int nb, const int* n, const double* const* d, const doubl
                        double* const* Z, const int* ldz, int* status, void* stream);
 
 /*
+ * Index partition for independent solves of one matrix, e.g. one part per
+ * GPU (the eigenpairs of an index range need no data from the other
+ * ranges).  Splits 1..n into nparts contiguous ranges il[p]..iu[p]
+ * (1-based, inclusive; il[p] = iu[p] + 1 for an empty part; il[0] = 1,
+ * iu[nparts-1] = n) whose boundaries lie where the classification of the
+ * root representation separates consecutive eigenvalues (Sec. 2,
+ * "Classification of the eigenvalues", with a margin of 4 gaptol), so that
+ * no cluster and no child representation is shared by two parts; each
+ * boundary is the separated pair nearest to the even split p n / nparts.
+ * Solving part p with mrrr_solve_s / _d (MRRR_INDEX, il[p]..iu[p], the same
+ * mode and params) gives eigenpairs that are mutually orthogonal with those
+ * of the other parts to the method's accuracy.  A matrix that splits into
+ * blocks is cut evenly.  d, e may be host or device pointers; il and iu are
+ * host arrays of nparts entries.  The work (root representation and
+ * bisection of the eigenvalues near the candidate boundaries) is enqueued on
+ * `stream` and the call returns when it is complete.
+ */
+int mrrr_partition_s(int n, const float* d, const float* e, mrrr_mode mode, const mrrr_params* params, int nparts,
+                     int* il, int* iu, void* stream);
+int mrrr_partition_d(int n, const double* d, const double* e, mrrr_mode mode, const mrrr_params* params,
+                     int nparts, int* il, int* iu, void* stream);
+
+/*
  * Eigenvectors for given eigenvalues without any device allocation.
  *
  * The paper has no counterpart of this entry point.  It is for callers that

@@ -98,6 +98,10 @@ def lib():
             f.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_int, ctypes.POINTER(MrrrParams), vp,
                           vp, vp, vp, vp, vp]
             f.restype = ctypes.c_int
+        for name in ("mrrr_partition_s", "mrrr_partition_d"):
+            f = getattr(L, name)
+            f.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.POINTER(MrrrParams), ctypes.c_int, vp, vp, vp]
+            f.restype = ctypes.c_int
         L.mrrr_eigvecs_noalloc_s.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
                                              vp]
         L.mrrr_eigvecs_noalloc_s.restype = ctypes.c_int
@@ -143,6 +147,14 @@ def mrrr_solve_batch_s(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, stat
 
 def mrrr_solve_batch_d(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, status, stream):
     return lib().mrrr_solve_batch_d(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, status, stream)
+
+
+def mrrr_partition_s(n, d, e, mode, params, nparts, il, iu, stream):
+    return lib().mrrr_partition_s(n, d, e, mode, params, nparts, il, iu, stream)
+
+
+def mrrr_partition_d(n, d, e, mode, params, nparts, il, iu, stream):
+    return lib().mrrr_partition_d(n, d, e, mode, params, nparts, il, iu, stream)
 
 
 def mrrr_eigvecs_noalloc_s(n, d, e, il, k, W, Z, ldz, stream):
@@ -304,6 +316,28 @@ def solve_batch(mats, mode="mixed", ranges=None, stream=None, timing=False, chec
         raise MrrrError(rc, "mrrr_solve_batch")
     out = [(Ws[i][:mout[i]], Zts[i][:mout[i]].T) for i in range(nb)]
     return out, stats.as_dict() | {"status": rc}, list(status)
+
+
+def partition(d, e, nparts, mode="mixed", stream=None, **param_kw):
+    """Index ranges (il, iu), 1-based inclusive, of nparts independent solves
+    of the tridiagonal (d, e) (mrrr_partition_s / _d); an empty part has
+    il = iu + 1."""
+    n = int(d.shape[0])
+    single = str(d.dtype).endswith("float32")
+    dev = _is_torch(d) and d.is_cuda
+    if not _is_torch(d):
+        d = np.ascontiguousarray(d)
+        e = np.ascontiguousarray(e) if e is not None else None
+    il = (ctypes.c_int * nparts)()
+    iu = (ctypes.c_int * nparts)()
+    prm = make_params(**param_kw)
+    fn = mrrr_partition_s if single else mrrr_partition_d
+    rc = fn(n, _ptr(d), _ptr(e) if (e is not None and n > 1) else None, MRRR_MIXED if mode == "mixed" else MRRR_PLAIN,
+            ctypes.byref(prm), nparts, ctypes.cast(il, ctypes.c_void_p), ctypes.cast(iu, ctypes.c_void_p),
+            _stream_handle(stream, dev))
+    if rc != MRRR_OK:
+        raise MrrrError(rc, "mrrr_partition")
+    return list(zip(list(il), list(iu)))
 
 
 class Server:

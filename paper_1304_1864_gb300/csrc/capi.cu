@@ -421,9 +421,147 @@ int solve_many(int nb, const int* n, const X* const* d, const X* const* e, const
     return MRRR_OK;
 }
 
+// Index partition of one tridiagonal for nparts independent solves (Sec. 2,
+// classification; the multi-GPU split of the wanted index range): parts are
+// contiguous index ranges whose boundaries lie where the root classification
+// separates consecutive eigenvalues, so that no cluster -- and no child
+// representation -- is shared by two parts.  For each interior target
+// t_p = round(p n / nparts) the root classification of a window of indices
+// around t_p is computed (one batched solve stopped after the root level,
+// each window an index range of the same matrix), and the boundary is put
+// after the index j nearest to t_p whose separation from j + 1 is at least
+// kCutMargin gaptol, considering only pairs whose own neighbours lie in the
+// window (their brackets are then those of a full solve).  Windows without
+// such a pair grow fourfold until they cover the matrix; a matrix that
+// splits into blocks is cut evenly (its blocks are independent).
+constexpr double kCutMargin = 4.0;
+
+template <class X>
+int partition_one(int n, const X* d, const X* e, mrrr_mode mode, const mrrr_params* prm, int nparts, int* il,
+                  int* iu, void* stream) {
+    const bool xs = std::is_same<X, float>::value;
+    if (n < 0 || nparts < 1 || !il || !iu || (mode != MRRR_PLAIN && mode != MRRR_MIXED)) return MRRR_ERR_ARG;
+    if (n > 0 && (!d || (n > 1 && !e))) return MRRR_ERR_ARG;
+    // even split first: the answer for small or split matrices
+    std::vector<int> cut(nparts + 1);
+    for (int p = 0; p <= nparts; ++p) cut[p] = (int)(((long long)n * p + nparts / 2) / nparts);
+    auto emit = [&]() {
+        for (int p = 0; p < nparts; ++p) {
+            il[p] = cut[p] + 1;
+            iu[p] = cut[p + 1];
+        }
+        return MRRR_OK;
+    };
+    if (nparts == 1 || n <= 2) return emit();
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+        cudaGetLastError();
+        return MRRR_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const mrrr::PtrKind kd = classify_ptr(d), ke = classify_ptr(e);
+    if (kd == PTR_OTHER_DEVICE || ke == PTR_OTHER_DEVICE) return MRRR_ERR_ARG;
+    DevBuf bd(st), be(st), bdummy(st);
+    const X* dd_ = d;
+    const X* de_ = e;
+    if (kd == PTR_HOST) {
+        if (!bd.alloc(sizeof(X) * n)) return MRRR_ERR_NOMEM;
+        if (cudaMemcpyAsync(bd.p, d, sizeof(X) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) return MRRR_ERR_CUDA;
+        dd_ = (const X*)bd.p;
+    }
+    if (ke == PTR_HOST) {
+        if (!be.alloc(sizeof(X) * (n - 1))) return MRRR_ERR_NOMEM;
+        if (cudaMemcpyAsync(be.p, e, sizeof(X) * (n - 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return MRRR_ERR_CUDA;
+        de_ = (const X*)be.p;
+    }
+    if (!bdummy.alloc(256)) return MRRR_ERR_NOMEM;  // W and Z are never written by a root-only solve
+    SolveCfg cfg = make_cfg(xs, mode == MRRR_MIXED, prm);
+    const double need = kCutMargin * cfg.gaptol;
+    std::vector<int> todo;  // interior targets still without a cut
+    for (int p = 1; p < nparts; ++p) todo.push_back(p);
+    std::vector<int> half(nparts, 32);
+    while (!todo.empty()) {
+        std::vector<MatrixDesc> mats;
+        for (int p : todo) {
+            MatrixDesc M;
+            memset(&M, 0, sizeof(M));
+            M.d = dd_;
+            M.e = de_;
+            M.W = bdummy.p;
+            M.Z = bdummy.p;
+            M.ldz = n;
+            M.n = n;
+            M.range = MRRR_INDEX;
+            M.il = std::max(1, cut[p] - half[p]);
+            M.iu = std::min(n, cut[p] + half[p]);
+            mats.push_back(M);
+        }
+        mrrr::RootSep rs;
+        const int P = (int)mats.size();
+        int rc;
+        if (xs)
+            rc = mode == MRRR_MIXED ? mrrr::solve_batch_s_mixed(P, mats.data(), cfg, 16, st, nullptr, &rs)
+                                    : mrrr::solve_batch_s_plain(P, mats.data(), cfg, 16, st, nullptr, &rs);
+        else
+            rc = mode == MRRR_MIXED ? mrrr::solve_batch_d_mixed(P, mats.data(), cfg, 16, st, nullptr, &rs)
+                                    : mrrr::solve_batch_d_plain(P, mats.data(), cfg, 16, st, nullptr, &rs);
+        if (rc != MRRR_OK) return rc;
+        for (int q = 0; q < P; ++q)
+            if (mats[q].status == mrrr::ST_ERR_NONFINITE) return MRRR_ERR_NONFINITE;
+        if (mats[0].nblocks > 1) break;  // blocks are independent: the even split stands
+        std::vector<int> next;
+        for (int q = 0; q < P; ++q) {
+            const int p = todo[q];
+            // items of window q, in index order (one block)
+            int best = -1;
+            long long bestd = 0;
+            const int K = (int)rs.j.size();
+            for (int t = 1; t + 2 < K; ++t) {
+                if (rs.matrix[t] != q || rs.matrix[t - 1] != q || rs.matrix[t + 2] != q) continue;
+                if (!(rs.rel[t] >= need)) continue;
+                const long long dist = std::llabs((long long)rs.j[t] - cut[p]);
+                if (best < 0 || dist < bestd) {
+                    best = rs.j[t];
+                    bestd = dist;
+                }
+            }
+            if (best >= 0) {
+                cut[p] = best;
+            } else if (2 * half[p] < n) {
+                half[p] *= 4;
+                next.push_back(p);
+            } else {
+                cut[p] = -1;  // no separated pair anywhere: this boundary merges with a neighbour
+            }
+        }
+        todo.swap(next);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MRRR_ERR_CUDA;
+    // boundaries without a cut, or out of order, collapse onto the previous one
+    cut[0] = 0;
+    cut[nparts] = n;
+    for (int p = 1; p < nparts; ++p)
+        if (cut[p] < cut[p - 1]) cut[p] = cut[p - 1];
+    for (int p = nparts - 1; p >= 1; --p)
+        if (cut[p] > cut[p + 1]) cut[p] = cut[p + 1];
+    return emit();
+}
+
 }  // namespace
 
 extern "C" {
+
+int mrrr_partition_s(int n, const float* d, const float* e, mrrr_mode mode, const mrrr_params* params, int nparts,
+                     int* il, int* iu, void* stream) {
+    return partition_one<float>(n, d, e, mode, params, nparts, il, iu, stream);
+}
+
+int mrrr_partition_d(int n, const double* d, const double* e, mrrr_mode mode, const mrrr_params* params,
+                     int nparts, int* il, int* iu, void* stream) {
+    return partition_one<double>(n, d, e, mode, params, nparts, il, iu, stream);
+}
+
 
 int mrrr_solve_batch_s(int nb, const int* n, const float* const* d, const float* const* e, const int* il,
                        const int* iu, mrrr_mode mode, const mrrr_params* params, int* m_out, float* const* W,

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "mrrr.h"
 #include "mrrr_types.cuh"
 
@@ -33,14 +35,27 @@ constexpr int kRqiTuneWarps[kRqiTuneCandidates] = {16, 8, 4};
 int rqi_tune_pick(unsigned key, int* trial);
 void rqi_tune_report(unsigned key, int trial, float ms);
 
+// The root-level classification of a batch (Algorithm 1, line 7, at the
+// root representation), for partitioning index ranges: a solve given a
+// RootSep stops after classifying the root level and returns, for every
+// eigenvalue item of every matrix in item order, the item's 1-based index j
+// within its block, its matrix and block, and the relative separation
+// reldist from the next item of the same block (+inf at the end of a block;
+// the classification separates the two where it is >= gaptol).  W and Z are
+// not touched.
+struct RootSep {
+    std::vector<int> j, matrix, block;
+    std::vector<double> rel;
+};
+
 // binary32 input/output: working precision binary64 (mixed) or binary32 (plain)
 int solve_batch_s_mixed(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
-                        mrrr_stats* stats);
+                        mrrr_stats* stats, RootSep* root_sep = nullptr);
 int solve_batch_s_plain(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
-                        mrrr_stats* stats);
+                        mrrr_stats* stats, RootSep* root_sep = nullptr);
 // binary64 input/output: working precision double-double (mixed) or binary64 (plain)
 int solve_batch_d_mixed(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
-                        mrrr_stats* stats);
+                        mrrr_stats* stats, RootSep* root_sep = nullptr);
 int solve_batch_d_plain(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
-                        mrrr_stats* stats);
+                        mrrr_stats* stats, RootSep* root_sep = nullptr);
 }  // namespace mrrr

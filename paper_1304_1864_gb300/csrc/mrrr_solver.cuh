@@ -821,7 +821,7 @@ struct TuneRun {
 
 template <class X, class Y>
 int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
-                mrrr_stats* stats) {
+                mrrr_stats* stats, RootSep* root_sep = nullptr) {
     typedef typename LowOf<Y>::T Lo;
     const bool use_low = LowOf<Y>::use && !(cfg.flags & MRRR_FLAG_NO_LOWPREC_BISECT);
     // relative width of the low-precision pre-bisection
@@ -894,7 +894,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
             // eigenvector columns of a split matrix are zero outside their block
             tl.begin(MRRR_PHASE_FINISH);
             int nz = 0;
-            for (int p = 0; p < P; ++p) {
+            for (int p = 0; p < P && !root_sep; ++p) {
                 if (mats[p].nblocks > 1 && mats[p].kout > 0) {
                     MRRR_CK(cudaMemset2DAsync(mats[p].Z, sizeof(X) * (size_t)mats[p].ldz, 0,
                                               sizeof(X) * (size_t)mats[p].n, mats[p].kout, st));
@@ -1022,6 +1022,30 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 tl.end();
                 MRRR_CK(cudaGetLastError());
                 if (int rc0 = from_device(ha, &C, d_C, 1, st)) return rc0;
+                if (level == 0 && root_sep) {
+                    // the root classification is all that was asked for
+                    std::vector<Item> hitems(K);
+                    if (int rc0 = from_device(ha, hitems.data(), items, (size_t)K, st)) return rc0;
+                    root_sep->j.resize(K);
+                    root_sep->matrix.resize(K);
+                    root_sep->block.resize(K);
+                    root_sep->rel.resize(K);
+                    for (int t = 0; t < K; ++t) {
+                        const Item& A = hitems[t];
+                        root_sep->j[t] = A.j;
+                        root_sep->matrix[t] = A.matrix;
+                        root_sep->block[t] = A.block;
+                        double rel = INFINITY;
+                        if (t + 1 < K && hitems[t + 1].block == A.block) {
+                            const Item& B = hitems[t + 1];
+                            const double den = std::max(std::max(fabs(A.lo), fabs(A.hi)), std::max(fabs(B.lo), fabs(B.hi)));
+                            rel = den > 0.0 ? (B.lo - A.hi) / den : 0.0;
+                        }
+                        root_sep->rel[t] = rel;
+                    }
+                    if (stats) tl.collect(stats);
+                    return MRRR_OK;
+                }
                 if (level == 0) {
                     s_root = C.nsingle;
                     if (C.ncluster > 0 && s_root > 0) {

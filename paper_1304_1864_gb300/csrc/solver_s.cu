@@ -4,11 +4,11 @@
 
 namespace mrrr {
 int solve_batch_s_mixed(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
-                        mrrr_stats* stats) {
-    return solve_batch<float, double>(P, mats, cfg, max_depth, st, stats);
+                        mrrr_stats* stats, RootSep* root_sep) {
+    return solve_batch<float, double>(P, mats, cfg, max_depth, st, stats, root_sep);
 }
 int solve_batch_s_plain(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cudaStream_t st,
-                        mrrr_stats* stats) {
-    return solve_batch<float, float>(P, mats, cfg, max_depth, st, stats);
+                        mrrr_stats* stats, RootSep* root_sep) {
+    return solve_batch<float, float>(P, mats, cfg, max_depth, st, stats, root_sep);
 }
 }  // namespace mrrr

@@ -103,3 +103,72 @@ def test_spectrum_generators_reach_their_spectrum(kind):
     assert np.array_equal(d, d2) and np.array_equal(e, e2)
     d3, _ = inputs.make(kind, n, seed=4)
     assert not np.array_equal(d, d3)
+
+
+def _cpu_part_solver(d, e, mode, il, iu):
+    # stand-in for the GPU solve of an index range (LAPACK, binary64), so that
+    # the sharding logic runs without a GPU
+    import torch
+    sl = pytest.importorskip("scipy.linalg")
+    w, v = sl.eigh_tridiagonal(d.numpy(), e.numpy(), select="i", select_range=(il - 1, iu - 1))
+    return torch.from_numpy(w), torch.from_numpy(np.ascontiguousarray(v))
+
+
+def _shard_worker(rank, world, port, parts, q):
+    import torch
+    import torch.distributed as dist
+    from paper_1304_1864_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    d, e = inputs.uniform_random(60, 9)
+    out = shard.solve_sharded(torch.from_numpy(d), torch.from_numpy(e), rank, world, gather="WZ",
+                              partitioner=lambda d_, e_, w_, m_: parts, solver=_cpu_part_solver)
+    q.put((rank, out["W"].numpy(), out["W_all"].numpy(), out["Z_all"].numpy()))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("parts", [[(1, 25), (26, 60)], [(1, 60), (61, 60)], [(1, 0), (1, 60)]],
+                         ids=["uneven", "empty-last", "empty-first"])
+def test_sharded_solve_gathers_two_gloo_ranks(parts):
+    # two CPU ranks, each solving its index range; the all-gathered W and Z
+    # are the parts in index order, identical on both ranks
+    import multiprocessing as mp
+    from paper_1304_1864_gb300 import shard
+    assert shard.check_parts(parts, 60)
+    ctx = mp.get_context("spawn")
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_shard_worker, args=(r, 2, port, parts, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    torch = pytest.importorskip("torch")
+    d, e = inputs.uniform_random(60, 9)
+    want_w, want_z = [], []
+    for a, b in parts:
+        if a <= b:
+            w, z = _cpu_part_solver(torch.from_numpy(d), torch.from_numpy(e), "mixed", a, b)
+            want_w.append(w.numpy())
+            want_z.append(z.numpy())
+    want_w = np.concatenate(want_w)
+    want_z = np.concatenate(want_z, axis=1)
+    for rank, w_own, w_all, z_all in out:
+        a, b = parts[rank]
+        assert w_own.size == max(b - a + 1, 0)
+        assert np.array_equal(w_all, want_w) and np.array_equal(z_all, want_z)
+
+
+def test_partition_helpers():
+    from paper_1304_1864_gb300 import shard
+    for n, world in [(10, 3), (1, 4), (0, 2), (4001, 8)]:
+        parts = shard.even_parts(n, world)
+        assert len(parts) == world and shard.check_parts(parts, n)
+    assert not shard.check_parts([(1, 5), (7, 10)], 10)
+    assert not shard.check_parts([(1, 5), (6, 9)], 10)
