@@ -98,6 +98,8 @@ typedef struct {
     double phase_ms[MRRR_NPHASES];    /* device time per phase (CUDA events on the solve's stream) */
     long long rqi_rows;   /* sum over all RQI steps of the order n of the step's block: each step is one
                              twisted factorization and solve of n rows (Sec. 2) */
+    int reps_backtracked; /* clusters processed again from the representation one level up because no
+                             candidate built from their parent passed (Sec. 3.2, "The representation tree") */
 } mrrr_stats;
 
 /* Tuning parameters; a zero field selects the default given in brackets. */
@@ -120,6 +122,9 @@ typedef struct {
 #define MRRR_FLAG_STRICT_GROWTH 8     /* MIXED: accept child reps only under the y = x growth bound,
                                          not the relaxed bound of Sec. 3.2, Eq. (3.6) */
 #define MRRR_FLAG_NO_TUNE 16          /* use the default RQI grid instead of the autotuned one */
+#define MRRR_FLAG_TEST_REJECT_CHILD 32 /* testing only: turn down every child representation built from a
+                                          parent that is itself a child, which forces the backtracking
+                                          branch of the representation tree (Sec. 3.2) */
 
 /*
  * Single-precision input/output (x = binary32).  MRRR_MIXED computes in

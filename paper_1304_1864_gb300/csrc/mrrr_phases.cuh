@@ -295,6 +295,9 @@ MRRR_HD void init_item(const BlockDesc& B, int bidx, Item& I, int t, const Y* re
     I.depth = 0;
     I.kind = KIND_OPEN;
     I.wanted = (I.j >= B.w_lo && I.j <= B.w_hi) ? 1 : 0;  // refined by assign_col
+    I.rep_up = nullptr;
+    I.sig_up_hi = 0.0;
+    I.sig_up_lo = 0.0;
     I.lam_hi = 0.0;
     I.lam_lo = 0.0;
     I.rqi_done = 0;
@@ -681,12 +684,22 @@ MRRR_HD double child_transform(const Y* parent, int n, Y tau, Y pm, Y* out, Lo* 
 // the spectrum (Sec. 3.2: a small gaptol leaves room to back off).  A
 // candidate is accepted when the element growth max |d+_i|, or else the
 // growth weighted by an approximate cluster vector, is at most
-// growth_k * spdiam(root).  If no candidate passes, the one with the
-// smallest weighted growth is taken (Sec. 2, "Requirements on the
-// representations"; Sec. 4.1) and counted in reps_failed.  In mixed precision
-// the plain growth test uses the relaxed bound of Eq. (3.6).  Members move to
-// the child: rep (and its low-precision copy), sigma += tau, brackets
-// shifted by -tau (re-verified by the refinement that follows).
+// growth_k * spdiam(root).  In mixed precision the plain growth test uses
+// the relaxed bound of Eq. (3.6).
+//
+// Backtracking (Sec. 3.2, "The representation tree": with a depth-first
+// order a cluster whose candidates all fail can be processed again "by
+// choosing different shifts at a higher level of the tree"): when no
+// candidate built from the parent passes and the parent is itself a child,
+// the same search runs on the representation one level up (the parent's
+// parent), with shifts next to this cluster instead of next to the larger
+// cluster the parent was made for; the child then hangs one level higher.
+// If that search fails too, the candidate with the smallest weighted growth
+// of both searches is taken and counted in reps_failed.
+//
+// Members move to the child: rep (and its low-precision copy), sigma +=
+// tau, brackets shifted into the child's coordinates (re-verified by the
+// refinement that follows).
 template <class Y, class Lo>
 MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* blocks, Y* pool, Lo* pool_lo,
                            const SolveCfg& cfg, DevCounters* C) {
@@ -694,77 +707,114 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     Item& first = items[K.a];
     Item& last = items[K.b - 1];
     const BlockDesc& B = blocks[first.block];
-    const Y* parent = (const Y*)first.rep;
     Y pm = from_d<Y>(B.pivmin);
     Y* child = pool + K.pool_off;
     Lo* child_lo = pool_lo + K.pool_off / 2;
-    double lo = first.lo, hi = last.hi;
-    double span = hi - lo;
-    double bw = fmax(first.hi - first.lo, last.hi - last.lo);
-    double base = fmax(fmax(0.25 * span, 2.0 * bw), 4.0 * cfg.eps_y * fmax(fabs(lo), fabs(hi)));
-    base = fmax(base, 4.0 * B.pivmin);
+    const double bw = fmax(first.hi - first.lo, last.hi - last.lo);
     const double bound = cfg.growth_k * B.spdiam;
     // Sec. 3.2, Eq. (3.6): with y > x the element growth may reach
     // max{10, eps_x / (eps_y sqrt(n))} spdiam without loss of accuracy
-    const double relaxed = (cfg.mixed && !(cfg.flags & 8 /* MRRR_FLAG_STRICT_GROWTH */))
+    const double relaxed = (cfg.mixed && !(cfg.flags & MRRR_FLAG_STRICT_GROWTH))
                                ? fmax(cfg.growth_k, cfg.eps_x / (cfg.eps_y * sqrt((double)n))) * B.spdiam
                                : bound;
-    double best_w = INFINITY, best_tau = lo - base;
-    double stored_tau = NAN;  // the candidate whose child rep is in `child`
-    bool accepted = false;
     unsigned long long steps = 0;
-    for (int k = 0; k < 6 && !accepted; ++k) {
-        double delta = base * (double)(1 << k);
-        for (int side = 0; side < 2 && !accepted; ++side) {
-            double gap = side == 0 ? K.gapL : K.gapR;
-            if (k > 0 && delta > 0.5 * gap) continue;
-            double tau = side == 0 ? lo - delta : hi + delta;
-            // the first candidate is usually accepted: build it in place
-            bool store = (k == 0 && side == 0);
-            double g = child_transform<Y, Lo>(parent, n, from_d<Y>(tau), pm, store ? child : (Y*)nullptr, child_lo);
-            if (store) stored_tau = tau;
-            steps += n;
-            if (g <= relaxed) {
-                best_tau = tau;
-                accepted = true;
-                if (g > bound) MRRR_ATOMIC_ADD(&C->reps_relaxed, 1);
-                break;
-            }
-            // child storage doubles as work space for the weighted test
-            double w = weighted_growth<Y>(parent, n, from_d<Y>(tau), pm, child);
-            stored_tau = NAN;
-            steps += 3ULL * n;
-            if (w <= bound) {
-                best_tau = tau;
-                accepted = true;
-                break;
-            }
-            if (w < best_w) {
-                best_w = w;
-                best_tau = tau;
+    struct Found {
+        bool accepted;
+        bool relaxed_only;
+        double tau, w;
+        double stored;  // the candidate whose child rep is in `child` (NaN: none)
+    };
+    // candidate search from `parent`, the cluster spanning [lo, hi] in its
+    // coordinates; `reject` turns every acceptance down (test hook)
+    auto search = [&](const Y* parent, double lo, double hi, bool reject) {
+        const double span = hi - lo;
+        double base = fmax(fmax(0.25 * span, 2.0 * bw), 4.0 * cfg.eps_y * fmax(fabs(lo), fabs(hi)));
+        base = fmax(base, 4.0 * B.pivmin);
+        Found f{false, false, lo - base, INFINITY, NAN};
+        for (int k = 0; k < 6 && !f.accepted; ++k) {
+            double delta = base * (double)(1 << k);
+            for (int side = 0; side < 2 && !f.accepted; ++side) {
+                double gap = side == 0 ? K.gapL : K.gapR;
+                if (k > 0 && delta > 0.5 * gap) continue;
+                double tau = side == 0 ? lo - delta : hi + delta;
+                // the first candidate is usually accepted: build it in place
+                bool store = (k == 0 && side == 0);
+                double g = child_transform<Y, Lo>(parent, n, from_d<Y>(tau), pm, store ? child : (Y*)nullptr,
+                                                  child_lo);
+                f.stored = store ? tau : f.stored;
+                steps += n;
+                if (!reject && g <= relaxed) {
+                    f.tau = tau;
+                    f.accepted = true;
+                    f.relaxed_only = g > bound;
+                    break;
+                }
+                // child storage doubles as work space for the weighted test
+                double w = weighted_growth<Y>(parent, n, from_d<Y>(tau), pm, child);
+                f.stored = NAN;
+                steps += 3ULL * n;
+                if (!reject && w <= bound) {
+                    f.tau = tau;
+                    f.accepted = true;
+                    break;
+                }
+                if (w < f.w) {
+                    f.w = w;
+                    f.tau = tau;
+                }
             }
         }
+        return f;
+    };
+    const Y* parent = (const Y*)first.rep;
+    // test hook: turn down every candidate built from a parent that is itself
+    // a child, so that the backtracking branch runs
+    const bool hook = (cfg.flags & MRRR_FLAG_TEST_REJECT_CHILD) && first.rep_up != nullptr;
+    Found f = search(parent, first.lo, last.hi, hook);
+    const Y* from = parent;
+    dd sig_from = dd(first.sig_hi, first.sig_lo);
+    double off = 0.0;  // coordinates of `from` minus those of the items' current rep
+    int depth = K.depth + 1;
+    if (!f.accepted && first.rep_up != nullptr) {
+        MRRR_ATOMIC_ADD(&C->reps_backtracked, 1);
+        const dd sig_up(first.sig_up_hi, first.sig_up_lo);
+        const dd d_off = dd(first.sig_hi, first.sig_lo) - sig_up;  // the shift that made the parent
+        const double o = d_off.hi + d_off.lo;
+        Found g = search((const Y*)first.rep_up, first.lo + o, last.hi + o, false);
+        if (g.accepted || g.w < f.w) {
+            f = g;
+            from = (const Y*)first.rep_up;
+            sig_from = sig_up;
+            off = o;
+            depth = K.depth;
+        }
+        f.stored = NAN;  // `child` may hold a candidate of either search
     }
-    if (!accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
-    if (!(stored_tau == best_tau)) {
-        child_transform<Y, Lo>(parent, n, from_d<Y>(best_tau), pm, child, child_lo);
+    if (!f.accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
+    if (f.accepted && f.relaxed_only) MRRR_ATOMIC_ADD(&C->reps_relaxed, 1);
+    if (!(f.stored == f.tau)) {
+        child_transform<Y, Lo>(from, n, from_d<Y>(f.tau), pm, child, child_lo);
         steps += n;
     }
     MRRR_ATOMIC_ADD(&C->qd_shift, steps);
-    // sigma_child = sigma_parent + tau, kept as an unevaluated double pair
-    dd sig = dd(first.sig_hi, first.sig_lo) + dd(best_tau);
+    // sigma_child = sigma_from + tau, kept as an unevaluated double pair
+    dd sig = sig_from + dd(f.tau);
+    const double move = off - f.tau;
     for (int u = K.a; u < K.b; ++u) {
         Item& I = items[u];
+        I.rep_up = from;
+        I.sig_up_hi = sig_from.hi;
+        I.sig_up_lo = sig_from.lo;
         I.rep = child;
         I.rep_lo = child_lo;
         I.sig_hi = sig.hi;
         I.sig_lo = sig.lo;
-        I.lo = I.lo - best_tau;
-        I.hi = I.hi - best_tau;
-        I.depth = K.depth + 1;
+        I.lo = I.lo + move;
+        I.hi = I.hi + move;
+        I.depth = depth;
         I.kind = KIND_OPEN;
     }
-    MRRR_ATOMIC_MAX(&C->d_max, K.depth + 1);
+    MRRR_ATOMIC_MAX(&C->d_max, depth);
 }
 
 // --------------------------------------------------------------- a6 + a7: RQI and store
@@ -777,7 +827,8 @@ MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratc
                                   int r_hint) {
 #if defined(__CUDA_ARCH__)
     if constexpr (std::is_same<Y, double>::value) {
-        if (Wk.stride == 1) return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax, r_hint);
+        if (Wk.stride == 1)
+            return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax, r_hint, Wk.nrld);
     }
 #endif
     // double-double, and the host build of binary64 (which follows the
@@ -891,7 +942,7 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
             // Rayleigh correction: allow one step more in this pass rather than
             // parking the eigenpair for a nearly empty later launch
             if (r_from_sweep && !final_pass && imax_t >= 0 && pass_iters < 3 &&
-                fabs(to_d(Wk.A(imax_t))) > 4.0)
+                (tr.zmax >= 0.0 ? tr.zmax : fabs(to_d(Wk.A(imax_t)))) > 4.0)
                 pass_iters = 3;
             if (tr.neg >= I.j) hi = bmin(hi, lam);
             else lo = bmax(lo, lam);
@@ -997,6 +1048,12 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     dd lt = dd(to_d(lam_out)) + dd(I.sig_hi, I.sig_lo);
     if constexpr (std::is_same<Y, dd>::value) lt = lam_out + dd(I.sig_hi, I.sig_lo);
     double lam_T = (lt.hi + lt.lo) / M.scale;
+    // a fused step left the chains' stored values in the scratch: scale them to z
+#if defined(__CUDA_ARCH__)
+    if constexpr (std::is_same<Y, double>::value) {
+        if (tr.fused) fused_finalize(Wk.a, n, tr);
+    }
+#endif
     // normalise, fix the sign (largest entry positive), cast to x, store
     A_t nrm = ysqrt(tr.nrm2);
     int imax = imax_t;

@@ -81,6 +81,10 @@ struct Item {
     int depth;          // depth of the current rep in the representation tree
     int kind;           // KIND_*
     int wanted;         // 1 if the eigenpair is returned, 0 if only a neighbour
+    // the representation one level up (the parent of `rep`; nullptr at the
+    // root) and its accumulated shift, for backtracking in the tree
+    const void* rep_up;
+    double sig_up_hi, sig_up_lo;
     // Rayleigh quotient iteration state carried between passes
     double lam_hi, lam_lo;  // current shift (hi + lo)
     int rqi_done;       // iterations done so far
@@ -120,6 +124,7 @@ struct DevCounters {
     int forced;
     int verify_fail;    // low-precision brackets that failed verification and were widened
     int reps_relaxed;   // child reps accepted only under the relaxed growth bound of Eq. (3.6)
+    int reps_backtracked;  // clusters processed again from the representation one level up
     int nrefine;        // items needing working-precision refinement at the current step
     int npark;          // eigenpairs parked for the next RQI pass
     int nvfix;          // items with a bracket end that failed its first check
