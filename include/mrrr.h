@@ -100,6 +100,9 @@ typedef struct {
                              twisted factorization and solve of n rows (Sec. 2) */
     int reps_backtracked; /* clusters processed again from the representation one level up because no
                              candidate built from their parent passed (Sec. 3.2, "The representation tree") */
+    int reps_krr_relaxed; /* (MRRR_FLAG_RRR_TEST) children accepted with a relative condition estimate above
+                             10, i.e. only under the relaxed k_rr bound of Eq. (3.7) */
+    double krr_max;       /* (MRRR_FLAG_RRR_TEST) largest relative condition estimate of an accepted child */
 } mrrr_stats;
 
 /* Tuning parameters; a zero field selects the default given in brackets. */
@@ -122,6 +125,14 @@ typedef struct {
 #define MRRR_FLAG_STRICT_GROWTH 8     /* MIXED: accept child reps only under the y = x growth bound,
                                          not the relaxed bound of Sec. 3.2, Eq. (3.6) */
 #define MRRR_FLAG_NO_TUNE 16          /* use the default RQI grid instead of the autotuned one */
+#define MRRR_FLAG_E_REP 64            /* e-representation (Sec. 3.2, "Choice of representations"): the root
+                                         keeps the input's off-diagonal e_i as data and every child keeps its
+                                         parent's LD_i = e_i exactly (stored once), instead of forming
+                                         LD = d l from its own pivots */
+#define MRRR_FLAG_RRR_TEST 128        /* accept a child representation only if the relative condition number
+                                         of the cluster's eigenvalues along an approximate cluster vector is
+                                         within the k_rr bound: 10, or with y > x the relaxed bound
+                                         max{10, eps_x gaptol / (eps_y sqrt(n))} of Sec. 3.2, Eq. (3.7) */
 #define MRRR_FLAG_TEST_REJECT_CHILD 32 /* testing only: turn down every child representation built from a
                                           parent that is itself a child, which forces the backtracking
                                           branch of the representation tree (Sec. 3.2) */

@@ -17,7 +17,7 @@ MRRR_PLAIN, MRRR_MIXED = 0, 1
 MRRR_OK, MRRR_ERR_ARG, MRRR_ERR_NONFINITE, MRRR_ERR_NOCONV = 0, -1, -2, -3
 MRRR_ERR_NOMEM, MRRR_ERR_CUDA, MRRR_ERR_TIMEOUT, MRRR_ERR_NOREP = -4, -5, -6, -7
 MRRR_FLAG_NO_LOWPREC_BISECT, MRRR_FLAG_TIMING, MRRR_FLAG_STRICT_GROWTH, MRRR_FLAG_NO_TUNE = 1, 4, 8, 16
-MRRR_FLAG_TEST_REJECT_CHILD = 32
+MRRR_FLAG_TEST_REJECT_CHILD, MRRR_FLAG_E_REP, MRRR_FLAG_RRR_TEST = 32, 64, 128
 NPHASES = 8
 PHASES = ("prep", "root", "bisect", "classify", "shift", "refine", "rqi", "finish")
 
@@ -31,7 +31,7 @@ class MrrrStats(ctypes.Structure):
                 ("reps_relaxed", ctypes.c_int), ("rqi_warps_per_sm", ctypes.c_int),
                 ("timed", ctypes.c_int), ("phase_launches", ctypes.c_int * NPHASES),
                 ("phase_ms", ctypes.c_double * NPHASES), ("rqi_rows", ctypes.c_longlong),
-                ("reps_backtracked", ctypes.c_int)]
+                ("reps_backtracked", ctypes.c_int), ("reps_krr_relaxed", ctypes.c_int), ("krr_max", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("phase_launches", "phase_ms")}

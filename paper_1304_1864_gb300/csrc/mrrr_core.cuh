@@ -303,9 +303,13 @@ MRRR_HD void perturb_and_derive(Y* rep, int n, double xi, uint64_t seed, uint64_
 
 // Stationary transform of the parent rep at shift tau.  If `out` is non-NULL
 // the child rep (D+, L+, LD+, LLD+) is written there.  Returns the element
-// growth max |d+_i|, or +inf if a non-finite value appeared.
+// growth max |d+_i|, or +inf if a non-finite value appeared.  With erep the
+// child is kept in e-representation (Sec. 3.2, "Choice of
+// representations"): a shift leaves the off-diagonal entries unchanged, so
+// the child's LD+ is the parent's LD, stored once and copied exactly, and
+// LLD+ = LD l+; otherwise LD+ = d+ l+ is formed from the child's own data.
 template <class Y>
-MRRR_HD double dstqds(const Y* parent, int n, Y tau, Y pivmin, Y* out) {
+MRRR_HD double dstqds(const Y* parent, int n, Y tau, Y pivmin, Y* out, bool erep = false) {
     RepPtr<Y> P(parent, n);
     Y s = -tau;
     double growth = 0.0;
@@ -320,8 +324,9 @@ MRRR_HD double dstqds(const Y* parent, int n, Y tau, Y pivmin, Y* out) {
         if (out) {
             out[i] = dp;
             out[n + i] = lp;
-            out[2 * n + i] = dp * lp;
-            out[3 * n + i] = dp * lp * lp;
+            const Y ldp = erep ? P.LD[i] : dp * lp;
+            out[2 * n + i] = ldp;
+            out[3 * n + i] = ldp * lp;
         }
     }
     Y dp = P.D[n - 1] + s;

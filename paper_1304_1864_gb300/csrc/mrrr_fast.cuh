@@ -252,8 +252,8 @@ __device__ __forceinline__ double stationary_fast(const double* __restrict__ D, 
 }
 
 static __device__ __noinline__ double dstqds_guarded(const double* parent, int n, double tau, double pivmin, double* out,
-                                             float* out_lo) {
-    double g = dstqds<double>(parent, n, tau, pivmin, out);
+                                             float* out_lo, bool erep) {
+    double g = dstqds<double>(parent, n, tau, pivmin, out, erep);
     if (out && g < INFINITY) {
         for (int i = 0; i < n; ++i) {
             out_lo[i] = (float)out[i];
@@ -269,7 +269,7 @@ static __device__ __noinline__ double dstqds_guarded(const double* parent, int n
 // in the same pass.  Unguarded; a vanished pivot makes the result
 // non-finite and the guarded generic transform is used instead.
 __device__ __forceinline__ double dstqds_fast(const double* __restrict__ parent, int n, double tau, double pivmin,
-                                              double* __restrict__ out, float* __restrict__ out_lo) {
+                                              double* __restrict__ out, float* __restrict__ out_lo, bool erep = false) {
     const double* __restrict__ D = parent;
     const double* __restrict__ L = parent + n;
     const double* __restrict__ LD = parent + 2 * n;
@@ -287,8 +287,8 @@ __device__ __forceinline__ double dstqds_fast(const double* __restrict__ parent,
         double lp = ldi * drcp<2>(dp);
         s = fma(lp * li, s, -tau);
         if (out) {
-            double ldp = dp * lp;
-            double lldp = ldp * lp;
+            const double ldp = erep ? ldi : dp * lp;  // e-representation: the parent's LD, exactly
+            const double lldp = ldp * lp;
             out[i] = dp;
             out[n + i] = lp;
             out[2 * n + i] = ldp;
@@ -301,7 +301,7 @@ __device__ __forceinline__ double dstqds_fast(const double* __restrict__ parent,
     unsigned long long a = dabsbits(dp);
     gmax = a > gmax ? a : gmax;
     if (!dfinite(s) || !dfinite(dp) || gmax >= 0x7ff0000000000000ULL)
-        return dstqds_guarded(parent, n, tau, pivmin, out, out_lo);
+        return dstqds_guarded(parent, n, tau, pivmin, out, out_lo, erep);
     if (out) {
         out[n - 1] = dp;
         out[2 * n - 1] = 0.0;
@@ -687,9 +687,7 @@ __device__ __forceinline__ TwistResult<double> twisted_fused_proj(const double* 
         A[st ? i : i + 1] = u;
         nrm = fma(u, u, nrm);
         const unsigned long long ua = dabsbits(u);
-        // top chain rows ascend, bottom rows descend: both keep the
-        // smallest row on ties
-        const bool better = st ? ua > umax : ua >= umax;
+        const bool better = ua > umax;
         umax = better ? ua : umax;
         ukmax = better ? k : ukmax;
         q *= m;
@@ -706,7 +704,10 @@ __device__ __forceinline__ TwistResult<double> twisted_fused_proj(const double* 
             q *= dpow2(-e);
             const unsigned qe = ((unsigned)__double2hiint(q) >> 20) & 0x7ffu;
             qbad |= (unsigned)(qe < 1023u - 900u);
-            if (qe > 1023u + 600u) {
+            // rare: a warp-uniform branch, so that the lanes that do not
+            // renormalise issue nothing for it
+            const bool big = qe > 1023u + 600u;
+            if (__any_sync(__activemask(), big) && big) {
                 q *= 0x1p-512;
                 nrm *= 0x1p-1024;
                 umax = (umax >> 52) > 512ULL ? umax - (512ULL << 52) : 0ULL;
@@ -715,7 +716,12 @@ __device__ __forceinline__ TwistResult<double> twisted_fused_proj(const double* 
                 brk1 = k + 1;
             }
         }
-        if (k + 1 == r) {  // the stationary rows are done: the progressive chain starts
+        // once per lane: the stationary rows are done, the progressive chain
+        // starts (a branch the warp skips together unless one of its lanes
+        // switches; lanes whose number of rows differs vote apart, which
+        // only costs the skip)
+        const bool sw = k + 1 == r;
+        if (__any_sync(__activemask(), sw) && sw) {
             Xtop = X;
             Ytop = Y;
             qtop = q;
@@ -780,8 +786,9 @@ __device__ __forceinline__ TwistResult<double> twisted_fused_proj(const double* 
     if (qbad | dnotnormal(Xtop) | dnotnormal(X) | !dfinite(gam) | !dfinite(nrm2) | !dfinite(ct) | !dfinite(cbt))
         return twisted_fixed_fallback(rep, n, lam, pivmin, A, B, gamma, imax, r);
     A[r] = 1.0;
-    // arg-max over the top chain, z_r = 1 and the bottom chain (smallest row
-    // on ties); the chains' maxima carry their renormalisation factor
+    // arg-max over the top chain, z_r = 1 and the bottom chain (on exact ties
+    // the first entry the walk reached); the chains' maxima carry their
+    // renormalisation factor
     const double zt = ukmax_top >= 0 ? __longlong_as_double((long long)umax_top) *
                                            chain_factor(ChainScale{fabs(ct), tbrk1, tbrk0, tcut}, ukmax_top)
                                      : -1.0;

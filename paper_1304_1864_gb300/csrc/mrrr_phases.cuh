@@ -7,6 +7,7 @@
 #include "mrrr_fast.cuh"
 #include "mrrr_types.cuh"
 
+#include <cstring>
 #include <type_traits>
 
 #if defined(__CUDA_ARCH__)
@@ -201,7 +202,7 @@ MRRR_HD void root_move(const BlockDesc& B, Y* reps, int i) {
 // identically alone and inside a batch.
 template <class Y, class Lo>
 MRRR_HD void root_element(const BlockDesc& B, const MatrixDesc& M, Y* reps, Lo* reps_lo, int i,
-                          const SolveCfg& cfg) {
+                          const SolveCfg& cfg, const double* we) {
     const int n = B.n;
     Y* rep = reps + 4 * (size_t)B.row0;
     Lo* lo = reps_lo + 2 * (size_t)B.row0;
@@ -209,13 +210,28 @@ MRRR_HD void root_element(const BlockDesc& B, const MatrixDesc& M, Y* reps, Lo* 
     uint64_t c0 = 4ULL * (uint64_t)B.mrow + 2ULL * (uint64_t)i;
     Y d = rep[i];
     Y l = (i < n - 1) ? rep[n + i] : from_d<Y>(0.0);
-    if (xi > 0.0) {
-        d = d + d * from_d<Y>(xi * sym_uniform(cfg.seed, c0));
-        if (i < n - 1) l = l + l * from_d<Y>(xi * sym_uniform(cfg.seed, c0 + 1ULL));
+    Y ld, lld;
+    if (cfg.flags & MRRR_FLAG_E_REP) {
+        // e-representation (Sec. 3.2, "Choice of representations"): the data
+        // are d_i and the off-diagonal e_i of T - mu I itself (the scaled
+        // input), perturbed by the same relative amounts; l_i = e_i / d_i
+        Y e = (i < n - 1) ? from_d<Y>(we[B.row0 + i]) : from_d<Y>(0.0);
+        if (xi > 0.0) {
+            d = d + d * from_d<Y>(xi * sym_uniform(cfg.seed, c0));
+            if (i < n - 1) e = e + e * from_d<Y>(xi * sym_uniform(cfg.seed, c0 + 1ULL));
+        }
+        l = (i < n - 1) ? e / d : from_d<Y>(0.0);
+        ld = e;
+        lld = e * l;
+    } else {
+        if (xi > 0.0) {
+            d = d + d * from_d<Y>(xi * sym_uniform(cfg.seed, c0));
+            if (i < n - 1) l = l + l * from_d<Y>(xi * sym_uniform(cfg.seed, c0 + 1ULL));
+        }
+        ld = d * l;
+        lld = ld * l;
     }
     rep[i] = d;
-    Y ld = d * l;
-    Y lld = ld * l;
     if (i < n - 1) {
         rep[n + i] = l;
         rep[2 * n + i] = ld;
@@ -635,9 +651,17 @@ MRRR_HD void classify_item(int t, Item* items, int K, double gaptol, int* single
 // dominated by the cluster's invariant subspace).  This weighs the element
 // growth by the vector it acts on, as conditional element growth does
 // (Definition "Conditional element growth", Sec. 2): a large pivot where the
-// eigenvector is negligible does no harm.  Uses `work` (3n words).
+// eigenvector is negligible does no harm.
+//
+// *kappa receives the relative condition number of the child's eigenvalue
+// along the same vector, the quantity relative robustness bounds (k_rr,
+// Definition of an RRR, Sec. 2): with y = L+^T z,
+//     kappa = sum_i |d+_i| y_i^2 / | sum_i d+_i y_i^2 |,
+// the relative change of the Rayleigh quotient z^T L+ D+ L+^T z under
+// element-wise relative perturbations of the d+_i (one for a definite
+// child).  Uses `work` (3n words).
 template <class Y>
-MRRR_HD double weighted_growth(const Y* parent, int n, Y tau, Y pm, Y* work) {
+MRRR_HD double weighted_growth(const Y* parent, int n, Y tau, Y pm, Y* work, double* kappa = nullptr) {
     Scratch<Y> Wk;
     Wk.a = work;
     Wk.b = work + n;
@@ -647,13 +671,26 @@ MRRR_HD double weighted_growth(const Y* parent, int n, Y tau, Y pm, Y* work) {
     double nrm2 = to_d(tr.nrm2);
     RepPtr<Y> P(parent, n);
     Y s = -tau;
-    double acc = 0.0;
+    double acc = 0.0, absq = 0.0, q = 0.0;
     for (int i = 0; i < n; ++i) {
         Y dp = P.D[i] + s;
         if (ysmall(dp, pm)) dp = -pm;
         double z = to_d(work[i]);
         acc += fabs(to_d(dp)) * z * z;
-        if (i < n - 1) s = qdiv<Y>(P.LD[i], dp) * P.L[i] * s - tau;
+        if (i < n - 1) {
+            const Y lp = qdiv<Y>(P.LD[i], dp);
+            const double y = z + to_d(lp) * to_d(work[i + 1]);
+            absq += fabs(to_d(dp)) * y * y;
+            q += to_d(dp) * y * y;
+            s = lp * P.L[i] * s - tau;
+        } else {
+            absq += fabs(to_d(dp)) * z * z;
+            q += to_d(dp) * z * z;
+        }
+    }
+    if (kappa) {
+        const double k = absq / fabs(q);
+        *kappa = isfinite(k) ? k : INFINITY;
     }
     double r = acc / nrm2;
     return isfinite(r) ? r : INFINITY;
@@ -662,12 +699,12 @@ MRRR_HD double weighted_growth(const Y* parent, int n, Y tau, Y pm, Y* work) {
 // Child rep parent - tau I and its rounded low-precision copy; returns the
 // element growth.  The device binary64 path builds both in one pass.
 template <class Y, class Lo>
-MRRR_HD double child_transform(const Y* parent, int n, Y tau, Y pm, Y* out, Lo* out_lo) {
+MRRR_HD double child_transform(const Y* parent, int n, Y tau, Y pm, Y* out, Lo* out_lo, bool erep) {
 #if defined(__CUDA_ARCH__)
     if constexpr (std::is_same<Y, double>::value && std::is_same<Lo, float>::value)
-        return dstqds_fast(parent, n, tau, to_d(pm), out, out_lo);
+        return dstqds_fast(parent, n, tau, to_d(pm), out, out_lo, erep);
 #endif
-    double g = dstqds<Y>(parent, n, tau, pm, out);
+    double g = dstqds<Y>(parent, n, tau, pm, out, erep);
     if (out) {
         for (int i = 0; i < n; ++i) {
             out_lo[i] = (Lo)to_d(out[i]);
@@ -718,11 +755,19 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
                                ? fmax(cfg.growth_k, cfg.eps_x / (cfg.eps_y * sqrt((double)n))) * B.spdiam
                                : bound;
     unsigned long long steps = 0;
+    const bool erep = (cfg.flags & MRRR_FLAG_E_REP) != 0;
+    // relative robustness (Sec. 3.2, Eq. (3.7)): with y > x the constant may
+    // reach max{10, eps_x gaptol / (eps_y sqrt(n))} without loss of accuracy
+    const bool rrtest = (cfg.flags & MRRR_FLAG_RRR_TEST) != 0;
+    const double krr_bound = (cfg.mixed && !(cfg.flags & MRRR_FLAG_STRICT_GROWTH))
+                                 ? fmax(10.0, cfg.eps_x * cfg.gaptol / (cfg.eps_y * sqrt((double)n)))
+                                 : 10.0;
     struct Found {
         bool accepted;
         bool relaxed_only;
         double tau, w;
         double stored;  // the candidate whose child rep is in `child` (NaN: none)
+        double kappa;   // relative condition estimate of the accepted child (-1: not measured)
     };
     // candidate search from `parent`, the cluster spanning [lo, hi] in its
     // coordinates; `reject` turns every acceptance down (test hook)
@@ -730,7 +775,7 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
         const double span = hi - lo;
         double base = fmax(fmax(0.25 * span, 2.0 * bw), 4.0 * cfg.eps_y * fmax(fabs(lo), fabs(hi)));
         base = fmax(base, 4.0 * B.pivmin);
-        Found f{false, false, lo - base, INFINITY, NAN};
+        Found f{false, false, lo - base, INFINITY, NAN, -1.0};
         for (int k = 0; k < 6 && !f.accepted; ++k) {
             double delta = base * (double)(1 << k);
             for (int side = 0; side < 2 && !f.accepted; ++side) {
@@ -740,22 +785,26 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
                 // the first candidate is usually accepted: build it in place
                 bool store = (k == 0 && side == 0);
                 double g = child_transform<Y, Lo>(parent, n, from_d<Y>(tau), pm, store ? child : (Y*)nullptr,
-                                                  child_lo);
+                                                  child_lo, erep);
                 f.stored = store ? tau : f.stored;
                 steps += n;
-                if (!reject && g <= relaxed) {
+                if (!reject && !rrtest && g <= relaxed) {
                     f.tau = tau;
                     f.accepted = true;
                     f.relaxed_only = g > bound;
                     break;
                 }
                 // child storage doubles as work space for the weighted test
-                double w = weighted_growth<Y>(parent, n, from_d<Y>(tau), pm, child);
+                double kappa = 0.0;
+                double w = weighted_growth<Y>(parent, n, from_d<Y>(tau), pm, child, &kappa);
                 f.stored = NAN;
                 steps += 3ULL * n;
-                if (!reject && w <= bound) {
+                const bool rr_ok = !rrtest || kappa <= krr_bound;
+                if (!reject && rr_ok && (g <= relaxed || w <= bound)) {
                     f.tau = tau;
                     f.accepted = true;
+                    f.relaxed_only = g > bound && w > bound;
+                    f.kappa = kappa;
                     break;
                 }
                 if (w < f.w) {
@@ -792,8 +841,16 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     }
     if (!f.accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
     if (f.accepted && f.relaxed_only) MRRR_ATOMIC_ADD(&C->reps_relaxed, 1);
+    if (f.kappa >= 0.0) {
+        // largest relative condition estimate of an accepted child (the bit
+        // patterns of non-negative doubles order like the values)
+        unsigned long long kb;
+        memcpy(&kb, &f.kappa, sizeof(kb));
+        MRRR_ATOMIC_MAX(&C->krr_max_bits, kb);
+        if (f.kappa > 10.0) MRRR_ATOMIC_ADD(&C->reps_krr_relaxed, 1);
+    }
     if (!(f.stored == f.tau)) {
-        child_transform<Y, Lo>(from, n, from_d<Y>(f.tau), pm, child, child_lo);
+        child_transform<Y, Lo>(from, n, from_d<Y>(f.tau), pm, child, child_lo, erep);
         steps += n;
     }
     MRRR_ATOMIC_ADD(&C->qd_shift, steps);

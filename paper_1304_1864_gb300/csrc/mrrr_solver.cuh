@@ -183,7 +183,7 @@ __global__ void k_root(const int* blist, BlockDesc* blocks, const MatrixDesc* ma
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) root_move<Y>(B, reps, i);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) root_element<Y, Lo>(B, M, reps, reps_lo, i, cfg);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) root_element<Y, Lo>(B, M, reps, reps_lo, i, cfg, we);
     __syncthreads();
     if (threadIdx.x == 0) root_range<Y>(B, M, wd, reps);
     if (nrld) {
@@ -1189,6 +1189,12 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         stats->rqi_warps_per_sm = rqi_wps;
         stats->rqi_rows = (long long)C.rqi_rows;
         stats->reps_backtracked = C.reps_backtracked;
+        stats->reps_krr_relaxed = C.reps_krr_relaxed;
+        {
+            double k;
+            memcpy(&k, &C.krr_max_bits, sizeof(k));
+            stats->krr_max = k;
+        }
         tl.collect(stats);
     }
     if (arena.failed) return MRRR_ERR_NOMEM;

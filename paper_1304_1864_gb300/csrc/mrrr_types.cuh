@@ -125,6 +125,8 @@ struct DevCounters {
     int verify_fail;    // low-precision brackets that failed verification and were widened
     int reps_relaxed;   // child reps accepted only under the relaxed growth bound of Eq. (3.6)
     int reps_backtracked;  // clusters processed again from the representation one level up
+    int reps_krr_relaxed;  // children accepted with a relative condition estimate above 10 (Eq. (3.7))
+    unsigned long long krr_max_bits;  // largest relative condition estimate of an accepted child (bits)
     int nrefine;        // items needing working-precision refinement at the current step
     int npark;          // eigenpairs parked for the next RQI pass
     int nvfix;          // items with a bracket end that failed its first check

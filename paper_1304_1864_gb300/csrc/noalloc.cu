@@ -153,7 +153,7 @@ __global__ void k_noalloc_root(unsigned char* base, const float* d, const float*
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) root_move<double>(B, rep, i);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) root_element<double, float>(B, M, rep, rep_lo, i, cfg);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) root_element<double, float>(B, M, rep, rep_lo, i, cfg, we);
     __syncthreads();
     const int w = threadIdx.x >> 5;  // warp 0: lambda_{il-1}, warp 1: lambda_{il+k}
     const int j = w == 0 ? il - 1 : il + k;

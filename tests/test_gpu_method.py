@@ -11,8 +11,13 @@
   no representation fails the acceptance test, in both precision pairs.
 * The variant paths: eigenvalues approximated only in the working precision
   (no lower-precision pre-bisection, the reading of Eq. (3.5) that needs no
-  verification) and the strict (y = x) element-growth bound instead of the
-  relaxed one of Eq. (3.6) -- each must meet the same accuracy targets.
+  verification), the strict (y = x) element-growth bound instead of the
+  relaxed one of Eq. (3.6), the e-representation of Sec. 3.2 ("Choice of
+  representations") and the relative-robustness acceptance test with the
+  relaxed k_rr bound of Eq. (3.7) -- each must meet the same accuracy
+  targets.
+* Backtracking in the representation tree (Sec. 3.2, "The representation
+  tree"), forced by a test hook.
 """
 import numpy as np
 import pytest
@@ -152,7 +157,7 @@ def test_tree_statistics_glued_wilkinson():
     assert 1 <= st["d_max"] <= 2
 
 
-VARIANTS = ["NO_LOWPREC_BISECT", "STRICT_GROWTH"]
+VARIANTS = ["NO_LOWPREC_BISECT", "STRICT_GROWTH", "E_REP", "RRR_TEST"]
 
 
 @pytest.mark.parametrize("flag", VARIANTS)
@@ -187,3 +192,38 @@ def test_variant_paths_n4001(flag):
         _acc.check_res_orth(d64, e64, W, Z, "s", "mixed")
         if flag == "NO_LOWPREC_BISECT":
             assert st["reps_failed"] == 0
+
+
+@pytest.mark.parametrize("prec", ["d", "s"])
+def test_backtracking_forced_by_the_test_hook(prec):
+    # plain MRRR (gaptol 1e-3) on twelve W_21 blocks glued together has
+    # clusters inside clusters (d_max >= 2).  The test hook turns down every
+    # child representation built from a child, so each such cluster must be
+    # processed again from the representation one level up (backtracking,
+    # Sec. 3.2, "The representation tree"); the results still meet the plain
+    # solver's targets and every eigenvalue matches the oracle.
+    import paper_1304_1864_gb300 as m
+    d, e = inputs.glued_wilkinson(12, 21, 1e-8 if prec == "d" else 1e-5)  # above the split threshold
+    d64, e64 = _acc.exact_input(d, e, prec)
+    W0, Z0, st0 = _solve(d, e, prec, "plain")
+    assert st0["d_max"] >= 2 and st0["reps_backtracked"] == 0, st0["d_max"]
+    W, Z, st = _solve(d, e, prec, "plain", flags=m.MRRR_FLAG_TEST_REJECT_CHILD)
+    assert st["reps_backtracked"] > 0 and st["reps_failed"] == 0, (st["reps_backtracked"], st["reps_failed"])
+    assert np.all(np.diff(W) >= 0)
+    _acc.check_eigvals(d64, e64, W, prec, "plain")
+    _acc.check_res_orth(d64, e64, W, Z, prec, "plain")
+
+
+def test_rrr_test_reports_the_relative_condition():
+    # with the relative-robustness test on, the n = 4001 Wilkinson matrix
+    # (about 2000 clusters of two) reports the largest relative condition
+    # estimate of its accepted children, which stays within the relaxed
+    # bound of Eq. (3.7) for binary32 in / binary64 inside
+    import paper_1304_1864_gb300 as m
+    d, e = inputs.workload_c2()[1]
+    W, Z, st = _solve(d, e, "s", "mixed", flags=m.MRRR_FLAG_RRR_TEST)
+    n = d.size
+    bound = max(10.0, 2.0 ** -24 * 1e-5 / (2.0 ** -53 * np.sqrt(n)))
+    print("krr_max %.3g, children above 10: %d, bound %.3g" % (st["krr_max"], st["reps_krr_relaxed"], bound))
+    assert st["nclusters"] > 0 and st["reps_failed"] == 0
+    assert 0.0 < st["krr_max"] <= bound
