@@ -351,9 +351,6 @@ template <class Y> struct Scratch {
     Y* a;
     Y* b;
     int stride;
-    // -1 / LD_i of the block's root representation (binary64 working
-    // precision only; nullptr: not available), for the fused twisted step
-    const double* nrld = nullptr;
     MRRR_HD Y& A(int i) const { return a[(size_t)i * stride]; }
     MRRR_HD Y& B(int i) const { return b[(size_t)i * stride]; }
 };
@@ -363,24 +360,10 @@ template <class Y> struct Scratch {
 template <class Y> struct Acc { typedef Y T; };
 template <> struct Acc<float> { typedef double T; };
 
-// Scale of the stored vector of one chain of the fused twisted step
-// (twisted_fused_proj): the value stored at walk step k, times c, is z at
-// that row -- except that values stored before a renormalisation of the
-// chain carry an extra factor 2^512 for each later renormalisation (steps
-// before brk1 take c 2^-512, steps before brk0 take c 2^-1024) and values
-// stored before `cut` are negligible (zero).  -1: no such renormalisation.
-struct ChainScale {
-    double c;
-    int brk1, brk0, cut;
-};
-
 template <class Y> struct TwistResult {
     int r;                     // twist index (0-based), argmin |gamma_k|, smallest k on ties
     int neg;                   // negative pivots of the stationary part = negcount(lambda)
     typename Acc<Y>::T nrm2;   // ||z||^2 (z_r = 1)
-    double zmax = -1.0;        // |z| at the arg-max (-1: not computed)
-    bool fused = false;        // the scratch holds the chains' stored values (see ChainScale), not z
-    ChainScale top, bot;       // (fused) scales of the rows above and below r
 };
 
 // One twisted-factorization solve at shift lam (Sec. 2, RQI steps (i)-(iii)):

@@ -70,13 +70,16 @@ __device__ __forceinline__ int dscale_exp(double x) {
 }
 __device__ __forceinline__ double dpow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
 
-// A projective pair is rescaled when |X| leaves [2^-256, 2^256): a row
-// changes |X| by the pivot d+_i, so X stays normal unless a single pivot is
-// below ~2^-760.  A zero or subnormal X (a vanished pivot) is left as it is:
-// the projective recurrences need no special case for it.
+// A projective pair of the twisted step is rescaled when |X| leaves
+// [2^-512, 2^512): a row changes |X| by the pivot d+_i, so X stays normal
+// unless a single pivot is below ~2^-510.  A zero or subnormal X (a vanished
+// pivot) is left as it is: the projective recurrences need no special case
+// for it.  The test is integer work on the high word; the rescale itself is
+// a branch the warp skips together unless one of its lanes needs it, since
+// a multiply under a false predicate still takes its full FP64 issue slot.
 __device__ __forceinline__ bool dneeds_rescale(double x) {
     const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
-    return e != 0u && e - (1023u - 256u) >= 512u;
+    return e != 0u && e - (1023u - 512u) >= 1024u;
 }
 // Sturm count (number of eigenvalues of L D L^T below tau) for bisection and
 // bracket checks, without a divide.  The stationary transform maps s_i to
@@ -443,7 +446,7 @@ constexpr int kGp = 4;
 // from the neighbouring multipliers), and the underflowed tail of a
 // localized vector stays zero.
 //
-// Where X leaves [2^-256, 2^256), X and Y are scaled by the power of two 2^k
+// Where X leaves [2^-512, 2^512), X and Y are scaled by the power of two 2^k
 // that brings X into [1, 2) -- the ratios and the signs do not change --
 // right after X was stored, so that both the decision and k follow from the
 // stored value itself; the solve, reaching that entry, multiplies its
@@ -473,7 +476,8 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
         const bool st = k < r;
         const int i = wrow(k);
         A[st ? i : i + 1] = X;
-        if (dneeds_rescale(X)) {
+        const bool rs = dneeds_rescale(X);
+        if (__any_sync(__activemask(), rs) && rs) {
             const double f = dpow2(dscale_exp(X));
             X *= f;
             Y *= f;
@@ -549,12 +553,15 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
         const int iz = sz(k);
         if (k == r) f = vr;  // the upward walk restarts at v_r
         f = -(l * f);
-        if (dneeds_rescale(a)) f *= dpow2(dscale_exp(a));
+        // the walk scaled X right after storing it: the same power of two,
+        // from the stored value (a warp-voted branch, as in the walk)
+        const bool rs = dneeds_rescale(a);
+        if (__any_sync(__activemask(), rs) && rs) f *= dpow2(dscale_exp(a));
         const double z = f * a;
         A[iz] = z;
         nrm2 = fma(z, z, nrm2);
         const unsigned long long za = dabsbits(z);
-        const bool better = za > zmax || (za == zmax && iz < im);
+        const bool better = za > zmax;
         zmax = better ? za : zmax;
         im = better ? iz : im;
     };
@@ -597,237 +604,6 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
     return res;
 }
 
-// Exponent k for which |x| 2^k lies in [1, 2), for rescaling a projective
-// pair together with the vector multiplier; 0 for a zero, subnormal or
-// non-finite x (left alone), clamped so that 2^k and 2^-k are both normal.
-__device__ __forceinline__ int dscale_exp_pair(double x) {
-    const int e = (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
-    return (e == 0 || e == 0x7ff) ? 0 : min(max(1023 - e, -1021), 1021);
-}
-
-// Factor of the value stored at walk step k of a chain (see ChainScale).
-__device__ __forceinline__ double chain_factor(const ChainScale& s, int k) {
-    return k < s.cut ? 0.0 : (k < s.brk0 ? s.c * 0x1p-1024 : (k < s.brk1 ? s.c * 0x1p-512 : s.c));
-}
-
-// The two-pass fixed-r step, out of line: the fused step's fallback for the
-// rare vectors it cannot scale.
-static __device__ __noinline__ TwistResult<double> twisted_fixed_fallback(const double* rep, int n, double lam,
-                                                                         double pivmin, double* A, double* B,
-                                                                         double* gamma, int* imax, int r) {
-    return twisted_fixed_proj(rep, n, lam, pivmin, A, B, gamma, imax, r);
-}
-
-// Fused twisted step at a given twist index r (Sec. 2, RQI steps (i)-(iii)):
-// the factorization and the vector in ONE pass over the rows, with no
-// second pass that reads the multipliers back.
-//
-// The projective walk is that of twisted_fixed_proj: r stationary rows
-// top-down (X = P_{i-1}, Y = N_i), then the progressive rows bottom-up
-// (X = R_{i+2}, Y = Q_{i+1}), one step X' = a X + Y, Y' = b Y - lam X'.
-// The vector is formed forward along the walk instead of backward from r.
-// Above r, N_r^T z = e_r gives z_i = prod_{j=i}^{r-1} (-l+_j) with
-// l+_j = ld_j P_{j-1} / P_j, hence
-//     z_i = C_top u_i,   u_i = P_{i-1} q_i,   q_i = prod_{j<i} (-1 / ld_j),
-// with the constant C_top = 1 / u_r fixed by z_r = 1; below r likewise
-//     z_i = C_bot w_i,   w_i = R_{i+1} q'_i,  q'_i = (-1)^i prod_{j=i}^{n-2} (1 / ld_j),
-// accumulated from the bottom (q'_{n-1} = (-1)^(n-1), q'_i = q'_{i+1} (-1 / ld_i))
-// and C_bot = 1 / w_r.  So each walk step stores
-// u (or w), accumulates its square for ||z||^2 and its magnitude for the
-// arg-max, and multiplies q by the precomputed -1/ld of its row: three FP64
-// instructions besides the three of the walk.  -1/ld is that of the root
-// representation of the block: a shift leaves the off-diagonal entries of
-// L D L^T unchanged (d+_i l+_i = d_i l_i), so a child's LD differs from the
-// root's only by the rounding of its own construction.
-//
-// Scaling: every sixteen steps X and Y are scaled by the power of two that
-// brings X into [1, 2) and q by its inverse (u = X q is unchanged).  u then
-// follows the magnitude of the vector itself, which grows towards r by up to
-// the full dynamic range of a localized eigenvector; when |q| exceeds 2^600
-// it is scaled by 2^-512, the squared norm by 2^-1024, and the step recorded
-// (ChainScale): values stored earlier take the factor 2^-512 per later
-// renormalisation, and from the third-last on they are negligible.  A q
-// that falls below 2^-900 (the vector dips by more than the exponent range
-// between two maxima), an overflow, or a vanished pivot at the twist sends
-// the step to the two-pass twisted_fixed_proj.
-//
-// The scratch then holds the stored values (A[r] = 1), to be scaled by
-// fused_finalize before it is read as z; ||z||^2, gamma_r, the inertia and
-// the arg-max of |z| are exact results of the step.
-__device__ __forceinline__ TwistResult<double> twisted_fused_proj(const double* __restrict__ rep,
-                                                                 const double* __restrict__ nrld, int n, double lam,
-                                                                 double pivmin, double* __restrict__ A,
-                                                                 double* __restrict__ B, double* gamma, int* imax,
-                                                                 int r) {
-    const double* __restrict__ D = rep;
-    const double* __restrict__ LLD = rep + 3 * n;
-    const double mlam = -lam;
-    const int steps = n - 1;
-    const double ylast = __ldg(D + n - 1) - lam;
-    const double qlast = (n - 1) & 1 ? -1.0 : 1.0;  // q'_{n-1} = (-1)^(n-1)
-    int neg = 0;
-    auto wrow = [&](int k) { return k < r ? k : n - 2 - (k - r); };
-    // current chain: walk state, vector multiplier, squared norm, arg-max
-    // (bits of the largest |u| and its walk step), renormalisation steps
-    double X = 1.0, Y = r > 0 ? mlam : ylast, q = r > 0 ? 1.0 : qlast, nrm = 0.0;
-    unsigned long long umax = 0;
-    int ukmax = -1;
-    int brk1 = -1, brk0 = -1, cut = -1;
-    unsigned qbad = 0u;
-    unsigned hx = (unsigned)__double2hiint(X);
-    // the finished top chain (r = 0: empty)
-    double Xtop = 1.0, Ytop = mlam, qtop = 1.0, nrm_top = 0.0;
-    unsigned long long umax_top = 0;
-    int ukmax_top = -1, tbrk1 = -1, tbrk0 = -1, tcut = -1;
-    const int full = steps - steps % kGp;
-    auto wstep = [&](int k, double a, double b, double m, bool scale) {
-        const bool st = k < r;
-        const int i = wrow(k);
-        const double u = X * q;
-        A[st ? i : i + 1] = u;
-        nrm = fma(u, u, nrm);
-        const unsigned long long ua = dabsbits(u);
-        const bool better = ua > umax;
-        umax = better ? ua : umax;
-        ukmax = better ? k : ukmax;
-        q *= m;
-        const double t = b * Y;
-        X = fma(a, X, Y);
-        const unsigned h = (unsigned)__double2hiint(X);
-        neg += (int)((h ^ hx) >> 31);
-        hx = h;
-        Y = fma(mlam, X, t);
-        if (scale) {
-            const int e = dscale_exp_pair(X);
-            X *= dpow2(e);
-            Y *= dpow2(e);
-            q *= dpow2(-e);
-            const unsigned qe = ((unsigned)__double2hiint(q) >> 20) & 0x7ffu;
-            qbad |= (unsigned)(qe < 1023u - 900u);
-            // rare: a warp-uniform branch, so that the lanes that do not
-            // renormalise issue nothing for it
-            const bool big = qe > 1023u + 600u;
-            if (__any_sync(__activemask(), big) && big) {
-                q *= 0x1p-512;
-                nrm *= 0x1p-1024;
-                umax = (umax >> 52) > 512ULL ? umax - (512ULL << 52) : 0ULL;
-                cut = brk0;
-                brk0 = brk1;
-                brk1 = k + 1;
-            }
-        }
-        // once per lane: the stationary rows are done, the progressive chain
-        // starts (a branch the warp skips together unless one of its lanes
-        // switches; lanes whose number of rows differs vote apart, which
-        // only costs the skip)
-        const bool sw = k + 1 == r;
-        if (__any_sync(__activemask(), sw) && sw) {
-            Xtop = X;
-            Ytop = Y;
-            qtop = q;
-            nrm_top = nrm;
-            umax_top = umax;
-            ukmax_top = ukmax;
-            tbrk1 = brk1;
-            tbrk0 = brk0;
-            tcut = cut;
-            X = 1.0;
-            Y = ylast;
-            q = qlast;
-            nrm = 0.0;
-            umax = 0;
-            ukmax = -1;
-            brk1 = brk0 = cut = -1;
-            hx = (unsigned)__double2hiint(X);
-        }
-    };
-    auto wload = [&](int k, double& a, double& b, double& m) {
-        const int kc = min(k, steps - 1);
-        const int i = wrow(kc);
-        const bool st = kc < r;
-        a = __ldg((st ? D : LLD) + i);
-        b = __ldg((st ? LLD : D) + i);
-        m = __ldg(nrld + i);
-    };
-    double ca[kGp], cb[kGp], cm[kGp], na[kGp], nb[kGp], nm[kGp];
-    if (full > 0) {
-#pragma unroll
-        for (int g = 0; g < kGp; ++g) wload(g, ca[g], cb[g], cm[g]);
-    }
-    for (int k0 = 0; k0 < full; k0 += kGp) {
-        {
-            const int ipf = wrow(min(k0 + kPrefetch, steps - 1));
-            pf_l2(D + ipf);
-            pf_l2(LLD + ipf);
-            pf_l2(nrld + ipf);
-        }
-#pragma unroll
-        for (int g = 0; g < kGp; ++g) wload(k0 + kGp + g, na[g], nb[g], nm[g]);
-#pragma unroll
-        for (int g = 0; g < kGp; ++g) wstep(k0 + g, ca[g], cb[g], cm[g], g == kGp - 1 && (k0 & 12) == 12);
-#pragma unroll
-        for (int g = 0; g < kGp; ++g) {
-            ca[g] = na[g];
-            cb[g] = nb[g];
-            cm[g] = nm[g];
-        }
-    }
-    for (int k = full; k < steps; ++k) {
-        double a, b, m;
-        wload(k, a, b, m);
-        wstep(k, a, b, m, false);
-    }
-    const double gam = Ytop / Xtop + Y / X + lam;
-    neg += dsign(gam);
-    const double ct = r > 0 ? 1.0 / (Xtop * qtop) : 0.0;
-    const double cbt = r < n - 1 ? 1.0 / (X * q) : 0.0;
-    const double st = sqrt(nrm_top) * fabs(ct), sb = sqrt(nrm) * fabs(cbt);
-    const double nrm2 = fma(st, st, fma(sb, sb, 1.0));
-    if (qbad | dnotnormal(Xtop) | dnotnormal(X) | !dfinite(gam) | !dfinite(nrm2) | !dfinite(ct) | !dfinite(cbt))
-        return twisted_fixed_fallback(rep, n, lam, pivmin, A, B, gamma, imax, r);
-    A[r] = 1.0;
-    // arg-max over the top chain, z_r = 1 and the bottom chain (on exact ties
-    // the first entry the walk reached); the chains' maxima carry their
-    // renormalisation factor
-    const double zt = ukmax_top >= 0 ? __longlong_as_double((long long)umax_top) *
-                                           chain_factor(ChainScale{fabs(ct), tbrk1, tbrk0, tcut}, ukmax_top)
-                                     : -1.0;
-    const double zb = ukmax >= 0 ? __longlong_as_double((long long)umax) *
-                                       chain_factor(ChainScale{fabs(cbt), brk1, brk0, cut}, ukmax)
-                                 : -1.0;
-    int im = r;
-    double zm = 1.0;
-    if (zt >= zm) {  // top rows lie above r
-        zm = zt;
-        im = ukmax_top;
-    }
-    if (zb > zm) {
-        zm = zb;
-        im = n - 1 - (ukmax - r);
-    }
-    *imax = im;
-    *gamma = gam;
-    TwistResult<double> res;
-    res.r = r;
-    res.neg = neg;
-    res.nrm2 = nrm2;
-    res.zmax = zm;
-    res.fused = true;
-    res.top = ChainScale{ct, tbrk1, tbrk0, tcut};
-    res.bot = ChainScale{cbt, brk1, brk0, cut};
-    return res;
-}
-
-// z from the values a fused step stored (in place): rows above r take the top
-// chain's factor of their walk step k = i, rows below r the bottom chain's,
-// whose walk step for row i is k = r + (n - 1 - i).
-__device__ __forceinline__ void fused_finalize(double* __restrict__ A, int n, const TwistResult<double>& tr) {
-    const int r = tr.r;
-    for (int i = 0; i < r; ++i) A[i] *= chain_factor(tr.top, i);
-    for (int i = r + 1; i < n; ++i) A[i] *= chain_factor(tr.bot, r + (n - 1 - i));
-    A[r] = 1.0;
-}
-
 // One twisted-factorization solve at lam for an eigenpair whose scratch
 // arrays A, B (n words each) are contiguous; same results contract as
 // twisted_solve: z in A (z_r = 1), returns r, inertia count and ||z||^2;
@@ -843,27 +619,10 @@ __device__ __forceinline__ void fused_finalize(double* __restrict__ A, int n, co
 // cases the inertia of Delta_r = diag(d+_0..d+_{r-1}, gamma_r,
 // w_{r+1}..w_{n-1}) is the Sturm count at lam (Sylvester), used to update
 // the bisection bracket.
-static __device__ __noinline__ TwistResult<double> twisted_full_fast(const double* __restrict__ rep, int n,
-                                                                    double lam, double pivmin, double* __restrict__ A,
-                                                                    double* __restrict__ B, double* gamma, int* imax,
-                                                                    int r_fixed);
-
 __device__ __forceinline__ TwistResult<double> twisted_solve_fast(const double* __restrict__ rep, int n, double lam,
                                                                  double pivmin, double* __restrict__ A,
                                                                  double* __restrict__ B, double* gamma, int* imax,
-                                                                 int r_fixed = -1,
-                                                                 const double* __restrict__ nrld = nullptr) {
-    if (r_fixed >= 0 && nrld) return twisted_fused_proj(rep, nrld, n, lam, pivmin, A, B, gamma, imax, r_fixed);
-    return twisted_full_fast(rep, n, lam, pivmin, A, B, gamma, imax, r_fixed);
-}
-
-// The full factorization (no twist index given) and the two-pass fixed-r
-// step, out of line so that the registers of the fused step's loop are not
-// set by them.
-static __device__ __noinline__ TwistResult<double> twisted_full_fast(const double* __restrict__ rep, int n,
-                                                                    double lam, double pivmin, double* __restrict__ A,
-                                                                    double* __restrict__ B, double* gamma, int* imax,
-                                                                    int r_fixed) {
+                                                                 int r_fixed = -1) {
     if (r_fixed >= 0) return twisted_fixed_proj(rep, n, lam, pivmin, A, B, gamma, imax, r_fixed);
     const double* __restrict__ D = rep;
     const double* __restrict__ L = rep + n;

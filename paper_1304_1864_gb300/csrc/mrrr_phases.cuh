@@ -314,6 +314,8 @@ MRRR_HD void init_item(const BlockDesc& B, int bidx, Item& I, int t, const Y* re
     I.rep_up = nullptr;
     I.sig_up_hi = 0.0;
     I.sig_up_lo = 0.0;
+    I.span_lo = 0.0;
+    I.span_hi = 0.0;
     I.lam_hi = 0.0;
     I.lam_lo = 0.0;
     I.rqi_done = 0;
@@ -624,7 +626,10 @@ MRRR_HD void classify_item(int t, Item* items, int K, double gaptol, int* single
     }
     int c = MRRR_ATOMIC_ADD(&C->ncluster, 1);
     int m0 = MRRR_ATOMIC_ADD(&C->nmember, e - t);
-    unsigned long long off = MRRR_ATOMIC_ADD(&C->pool_need, 4ULL * (unsigned long long)I.n);
+    // a cluster whose rep is itself a child gets a second slot, for the
+    // alternative parent rep of backtracking (shift_cluster)
+    const unsigned long long slots = I.rep_up ? 2ULL : 1ULL;
+    unsigned long long off = MRRR_ATOMIC_ADD(&C->pool_need, slots * 4ULL * (unsigned long long)I.n);
     Cluster& Kc = clusters[c];
     Kc.a = t;
     Kc.b = e;
@@ -722,17 +727,19 @@ MRRR_HD double child_transform(const Y* parent, int n, Y tau, Y pm, Y* out, Lo* 
 // candidate is accepted when the element growth max |d+_i|, or else the
 // growth weighted by an approximate cluster vector, is at most
 // growth_k * spdiam(root).  In mixed precision the plain growth test uses
-// the relaxed bound of Eq. (3.6).
+// the relaxed bound of Eq. (3.6); MRRR_FLAG_RRR_TEST adds the relative
+// robustness test with the k_rr bound of Eq. (3.7).
 //
-// Backtracking (Sec. 3.2, "The representation tree": with a depth-first
-// order a cluster whose candidates all fail can be processed again "by
-// choosing different shifts at a higher level of the tree"): when no
-// candidate built from the parent passes and the parent is itself a child,
-// the same search runs on the representation one level up (the parent's
-// parent), with shifts next to this cluster instead of next to the larger
-// cluster the parent was made for; the child then hangs one level higher.
-// If that search fails too, the candidate with the smallest weighted growth
-// of both searches is taken and counted in reps_failed.
+// Backtracking (Sec. 3.2, "The representation tree": a cluster whose
+// candidates all fail can be processed again "by choosing different shifts
+// at a higher level of the tree"): when no candidate built from the parent
+// P passes and P is itself a child -- made from its own parent G for a
+// cluster spanning [span_lo, span_hi] of G -- the candidate search for that
+// cluster is run again from G, skipping the shift that made P, and gives an
+// alternative parent P' (kept in a second pool slot of this cluster); the
+// cluster's members move to P' and the search for their child runs there.
+// If that fails too, the candidate with the smallest weighted growth of the
+// searches is taken and counted in reps_failed.
 //
 // Members move to the child: rep (and its low-precision copy), sigma +=
 // tau, brackets shifted into the child's coordinates (re-verified by the
@@ -747,7 +754,6 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     Y pm = from_d<Y>(B.pivmin);
     Y* child = pool + K.pool_off;
     Lo* child_lo = pool_lo + K.pool_off / 2;
-    const double bw = fmax(first.hi - first.lo, last.hi - last.lo);
     const double bound = cfg.growth_k * B.spdiam;
     // Sec. 3.2, Eq. (3.6): with y > x the element growth may reach
     // max{10, eps_x / (eps_y sqrt(n))} spdiam without loss of accuracy
@@ -766,12 +772,15 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
         bool accepted;
         bool relaxed_only;
         double tau, w;
-        double stored;  // the candidate whose child rep is in `child` (NaN: none)
-        double kappa;   // relative condition estimate of the accepted child (-1: not measured)
+        double stored;  // the candidate whose rep is in the output slot (NaN: none)
+        double kappa;   // relative condition estimate of the accepted candidate (-1: not measured)
     };
-    // candidate search from `parent`, the cluster spanning [lo, hi] in its
-    // coordinates; `reject` turns every acceptance down (test hook)
-    auto search = [&](const Y* parent, double lo, double hi, bool reject) {
+    // candidate search from `parent` for a cluster spanning [lo, hi] in its
+    // coordinates with bracket width bw; the candidate reps are built into
+    // `out` (which doubles as work space); `reject` turns every acceptance
+    // down (test hook); the candidate `skip` is not tried
+    auto search = [&](const Y* parent, double lo, double hi, double bw, Y* out, Lo* out_lo, bool reject,
+                      double skip) {
         const double span = hi - lo;
         double base = fmax(fmax(0.25 * span, 2.0 * bw), 4.0 * cfg.eps_y * fmax(fabs(lo), fabs(hi)));
         base = fmax(base, 4.0 * B.pivmin);
@@ -782,10 +791,11 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
                 double gap = side == 0 ? K.gapL : K.gapR;
                 if (k > 0 && delta > 0.5 * gap) continue;
                 double tau = side == 0 ? lo - delta : hi + delta;
+                if (tau == skip) continue;
                 // the first candidate is usually accepted: build it in place
-                bool store = (k == 0 && side == 0);
-                double g = child_transform<Y, Lo>(parent, n, from_d<Y>(tau), pm, store ? child : (Y*)nullptr,
-                                                  child_lo, erep);
+                bool store = !(f.stored == f.stored);
+                double g = child_transform<Y, Lo>(parent, n, from_d<Y>(tau), pm, store ? out : (Y*)nullptr,
+                                                  out_lo, erep);
                 f.stored = store ? tau : f.stored;
                 steps += n;
                 if (!reject && !rrtest && g <= relaxed) {
@@ -794,9 +804,8 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
                     f.relaxed_only = g > bound;
                     break;
                 }
-                // child storage doubles as work space for the weighted test
                 double kappa = 0.0;
-                double w = weighted_growth<Y>(parent, n, from_d<Y>(tau), pm, child, &kappa);
+                double w = weighted_growth<Y>(parent, n, from_d<Y>(tau), pm, out, &kappa);
                 f.stored = NAN;
                 steps += 3ULL * n;
                 const bool rr_ok = !rrtest || kappa <= krr_bound;
@@ -815,27 +824,42 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
         }
         return f;
     };
+    const double bw = fmax(first.hi - first.lo, last.hi - last.lo);
     const Y* parent = (const Y*)first.rep;
+    dd sig_from = dd(first.sig_hi, first.sig_lo);
+    const Y* from = parent;
+    const void* from_up = first.rep_up;  // the parent's own parent (for the members' rep_up)
+    dd sig_up = dd(first.sig_up_hi, first.sig_up_lo);
+    double move = 0.0;  // shift of the members' brackets into the coordinates of `from`
     // test hook: turn down every candidate built from a parent that is itself
     // a child, so that the backtracking branch runs
     const bool hook = (cfg.flags & MRRR_FLAG_TEST_REJECT_CHILD) && first.rep_up != nullptr;
-    Found f = search(parent, first.lo, last.hi, hook);
-    const Y* from = parent;
-    dd sig_from = dd(first.sig_hi, first.sig_lo);
-    double off = 0.0;  // coordinates of `from` minus those of the items' current rep
-    int depth = K.depth + 1;
+    Found f = search(parent, first.lo, last.hi, bw, child, child_lo, hook, NAN);
     if (!f.accepted && first.rep_up != nullptr) {
+        // backtracking: another rep for the parent's cluster, from the
+        // parent's parent G, skipping the shift that made the parent
         MRRR_ATOMIC_ADD(&C->reps_backtracked, 1);
-        const dd sig_up(first.sig_up_hi, first.sig_up_lo);
-        const dd d_off = dd(first.sig_hi, first.sig_lo) - sig_up;  // the shift that made the parent
-        const double o = d_off.hi + d_off.lo;
-        Found g = search((const Y*)first.rep_up, first.lo + o, last.hi + o, false);
+        const Y* G = (const Y*)first.rep_up;
+        const dd tp = dd(first.sig_hi, first.sig_lo) - sig_up;  // the shift that made P from G
+        const double tau_p = tp.hi + tp.lo;
+        Y* alt = child + 4 * (size_t)n;
+        Lo* alt_lo = child_lo + 2 * (size_t)n;
+        const double pw = fmax(bw, 1e-3 * (first.span_hi - first.span_lo));
+        Found fp = search(G, first.span_lo, first.span_hi, pw, alt, alt_lo, false, tau_p);
+        if (!(fp.stored == fp.tau)) child_transform<Y, Lo>(G, n, from_d<Y>(fp.tau), pm, alt, alt_lo, erep);
+        steps += n;
+        if (!fp.accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
+        // the members in the coordinates of P' = G - tau' I: + tau_p - tau'
+        const double mv = tau_p - fp.tau;
+        Found g = search(alt, first.lo + mv, last.hi + mv, bw, child, child_lo, false, NAN);
         if (g.accepted || g.w < f.w) {
             f = g;
-            from = (const Y*)first.rep_up;
-            sig_from = sig_up;
-            off = o;
-            depth = K.depth;
+            from = alt;
+            from_up = G;
+            sig_from = sig_up + dd(fp.tau);
+            move = mv;
+            // P' is the members' new parent rep: it was made for the
+            // parent's cluster, whose span stays the same in G
         }
         f.stored = NAN;  // `child` may hold a candidate of either search
     }
@@ -855,23 +879,26 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     }
     MRRR_ATOMIC_ADD(&C->qd_shift, steps);
     // sigma_child = sigma_from + tau, kept as an unevaluated double pair
-    dd sig = sig_from + dd(f.tau);
-    const double move = off - f.tau;
+    const dd sig = sig_from + dd(f.tau);
+    const double span_lo = first.lo + move, span_hi = last.hi + move;  // this cluster, in `from`
+    (void)from_up;
     for (int u = K.a; u < K.b; ++u) {
         Item& I = items[u];
+        I.lo = I.lo + move - f.tau;
+        I.hi = I.hi + move - f.tau;
         I.rep_up = from;
         I.sig_up_hi = sig_from.hi;
         I.sig_up_lo = sig_from.lo;
+        I.span_lo = span_lo;
+        I.span_hi = span_hi;
         I.rep = child;
         I.rep_lo = child_lo;
         I.sig_hi = sig.hi;
         I.sig_lo = sig.lo;
-        I.lo = I.lo + move;
-        I.hi = I.hi + move;
-        I.depth = depth;
+        I.depth = K.depth + 1;
         I.kind = KIND_OPEN;
     }
-    MRRR_ATOMIC_MAX(&C->d_max, depth);
+    MRRR_ATOMIC_MAX(&C->d_max, K.depth + 1);
 }
 
 // --------------------------------------------------------------- a6 + a7: RQI and store
@@ -884,8 +911,7 @@ MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratc
                                   int r_hint) {
 #if defined(__CUDA_ARCH__)
     if constexpr (std::is_same<Y, double>::value) {
-        if (Wk.stride == 1)
-            return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax, r_hint, Wk.nrld);
+        if (Wk.stride == 1) return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax, r_hint);
     }
 #endif
     // double-double, and the host build of binary64 (which follows the
@@ -999,7 +1025,7 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
             // Rayleigh correction: allow one step more in this pass rather than
             // parking the eigenpair for a nearly empty later launch
             if (r_from_sweep && !final_pass && imax_t >= 0 && pass_iters < 3 &&
-                (tr.zmax >= 0.0 ? tr.zmax : fabs(to_d(Wk.A(imax_t)))) > 4.0)
+                fabs(to_d(Wk.A(imax_t))) > 4.0)
                 pass_iters = 3;
             if (tr.neg >= I.j) hi = bmin(hi, lam);
             else lo = bmax(lo, lam);
@@ -1105,12 +1131,6 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
     dd lt = dd(to_d(lam_out)) + dd(I.sig_hi, I.sig_lo);
     if constexpr (std::is_same<Y, dd>::value) lt = lam_out + dd(I.sig_hi, I.sig_lo);
     double lam_T = (lt.hi + lt.lo) / M.scale;
-    // a fused step left the chains' stored values in the scratch: scale them to z
-#if defined(__CUDA_ARCH__)
-    if constexpr (std::is_same<Y, double>::value) {
-        if (tr.fused) fused_finalize(Wk.a, n, tr);
-    }
-#endif
     // normalise, fix the sign (largest entry positive), cast to x, store
     A_t nrm = ysqrt(tr.nrm2);
     int imax = imax_t;

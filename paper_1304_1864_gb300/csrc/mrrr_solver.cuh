@@ -136,7 +136,7 @@ __global__ void k_prep(MatrixDesc* mats, BlockDesc* blocks, double* wd, double* 
 // perturbation and derived data on all threads.
 template <class Y, class Lo>
 __global__ void k_root(const int* blist, BlockDesc* blocks, const MatrixDesc* mats, const double* wd,
-                       const double* we, Y* reps, Lo* reps_lo, SolveCfg cfg, double* nrld) {
+                       const double* we, Y* reps, Lo* reps_lo, SolveCfg cfg) {
     constexpr int T = kRootThreads;
     __shared__ double s_gl, s_gu, s_g[2], s_mu[2];
     __shared__ double r_gl[T], r_gu[T], r_e2[T];
@@ -170,7 +170,6 @@ __global__ void k_root(const int* blist, BlockDesc* blocks, const MatrixDesc* ma
         if (threadIdx.x == 0) {
             root_trivial<Y, Lo>(B, wd, reps, reps_lo);
             root_range<Y>(B, M, wd, reps);
-            if (nrld) nrld[B.row0] = 0.0;
         }
         return;
     }
@@ -186,13 +185,6 @@ __global__ void k_root(const int* blist, BlockDesc* blocks, const MatrixDesc* ma
     for (int i = threadIdx.x; i < n; i += blockDim.x) root_element<Y, Lo>(B, M, reps, reps_lo, i, cfg, we);
     __syncthreads();
     if (threadIdx.x == 0) root_range<Y>(B, M, wd, reps);
-    if (nrld) {
-        // -1 / LD_i of the root rep, for the fused twisted step (a shift keeps
-        // the off-diagonal entries, so the children of this block share it)
-        const Y* rep = reps + 4 * (size_t)B.row0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
-            nrld[B.row0 + i] = i < n - 1 ? -1.0 / to_d(rep[2 * n + i]) : 0.0;
-    }
 }
 
 // Exclusive scan of the item counts over the block list (one CTA), plus the
@@ -536,7 +528,7 @@ __global__ void k_shift(const Cluster* clusters, int nc, Item* items, const Bloc
 template <class X, class Y>
 __global__ void k_rqi(Item* items, const int* list, int count, const int* dev_total, int* queue, MatrixDesc* mats,
                       const BlockDesc* blocks, SolveCfg cfg, Y* scratch, int nmax, DevCounters* C, int pass_iters,
-                      int final_pass, int* park_list, int* park_count, const double* nrld) {
+                      int final_pass, int* park_list, int* park_count) {
     constexpr bool kCoop = !std::is_same<Y, dd>::value;
     __shared__ X tile[32][33];
     const int lane = threadIdx.x & 31;
@@ -561,7 +553,6 @@ __global__ void k_rqi(Item* items, const int* list, int count, const int* dev_to
         bool stored = false;
         if (active) {
             Item& I = items[it];
-            Wk.nrld = nrld ? nrld + blocks[I.block].row0 : nullptr;
             stored = rqi_item<X, Y>(I, mats, blocks, cfg, Wk, C, pass_iters, final_pass != 0,
                                     kCoop ? &scale : nullptr);
             if (!stored) {
@@ -855,12 +846,6 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
     MRRR_ALLOC(we, double, N);
     MRRR_ALLOC(reps, Y, 4 * N);
     MRRR_ALLOC(reps_lo, Lo, 2 * N);
-    // -1 / LD of the root reps for the fused twisted step (binary64 working precision)
-    double* nrld = nullptr;
-    if (std::is_same<Y, double>::value) {
-        nrld = arena.alloc<double>(N);
-        if (!nrld) return MRRR_ERR_NOMEM;
-    }
     MRRR_ALLOC(d_C, DevCounters, 1);
     MRRR_ALLOC(d_total, int, 1);
     MRRR_CK(cudaMemsetAsync(d_C, 0, sizeof(DevCounters), st));
@@ -885,7 +870,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
         if (int rc0 = to_device(ha, d_blist, blist.data(), (size_t)NB, st)) return rc0;
         // a2: root representations
         tl.begin(MRRR_PHASE_ROOT);
-        k_root<Y, Lo><<<NB, kRootThreads, 0, st>>>(d_blist, d_blocks, d_mats, wd, we, reps, reps_lo, cfg, nrld);
+        k_root<Y, Lo><<<NB, kRootThreads, 0, st>>>(d_blist, d_blocks, d_mats, wd, we, reps, reps_lo, cfg);
         k_scan_items<<<1, 1024, 0, st>>>(d_blist, NB, d_blocks, d_mats, P, d_total);
         tl.end(2);
         MRRR_CK(cudaGetLastError());
@@ -1006,8 +991,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                     int iters = pass == 0 ? 2 : (final_pass ? cfg.max_rqi : 3);
                     tl.begin(MRRR_PHASE_RQI, rs);
                     k_rqi<X, Y><<<(int)G, 32, 0, rs>>>(items, list, S, total, queues + pass, d_mats, d_blocks, cfg,
-                                                        scratch, nmax, d_C, iters, final_pass ? 1 : 0, out, cnt,
-                                                        nrld);
+                                                        scratch, nmax, d_C, iters, final_pass ? 1 : 0, out, cnt);
                     tl.end(1, rs);
                     if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
                     list = out;
