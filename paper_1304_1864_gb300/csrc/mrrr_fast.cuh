@@ -70,16 +70,13 @@ __device__ __forceinline__ int dscale_exp(double x) {
 }
 __device__ __forceinline__ double dpow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
 
-// A projective pair of the twisted step is rescaled when |X| leaves
-// [2^-512, 2^512): a row changes |X| by the pivot d+_i, so X stays normal
-// unless a single pivot is below ~2^-510.  A zero or subnormal X (a vanished
-// pivot) is left as it is: the projective recurrences need no special case
-// for it.  The test is integer work on the high word; the rescale itself is
-// a branch the warp skips together unless one of its lanes needs it, since
-// a multiply under a false predicate still takes its full FP64 issue slot.
+// A projective pair is rescaled when |X| leaves [2^-256, 2^256): a row
+// changes |X| by the pivot d+_i, so X stays normal unless a single pivot is
+// below ~2^-760.  A zero or subnormal X (a vanished pivot) is left as it is:
+// the projective recurrences need no special case for it.
 __device__ __forceinline__ bool dneeds_rescale(double x) {
     const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
-    return e != 0u && e - (1023u - 512u) >= 1024u;
+    return e != 0u && e - (1023u - 256u) >= 512u;
 }
 // Sturm count (number of eigenvalues of L D L^T below tau) for bisection and
 // bracket checks, without a divide.  The stationary transform maps s_i to
@@ -476,8 +473,7 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
         const bool st = k < r;
         const int i = wrow(k);
         A[st ? i : i + 1] = X;
-        const bool rs = dneeds_rescale(X);
-        if (__any_sync(__activemask(), rs) && rs) {
+        if (dneeds_rescale(X)) {
             const double f = dpow2(dscale_exp(X));
             X *= f;
             Y *= f;
@@ -553,15 +549,12 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
         const int iz = sz(k);
         if (k == r) f = vr;  // the upward walk restarts at v_r
         f = -(l * f);
-        // the walk scaled X right after storing it: the same power of two,
-        // from the stored value (a warp-voted branch, as in the walk)
-        const bool rs = dneeds_rescale(a);
-        if (__any_sync(__activemask(), rs) && rs) f *= dpow2(dscale_exp(a));
+        if (dneeds_rescale(a)) f *= dpow2(dscale_exp(a));
         const double z = f * a;
         A[iz] = z;
         nrm2 = fma(z, z, nrm2);
         const unsigned long long za = dabsbits(z);
-        const bool better = za > zmax;
+        const bool better = za > zmax || (za == zmax && iz < im);
         zmax = better ? za : zmax;
         im = better ? iz : im;
     };
