@@ -463,9 +463,7 @@ def run_ours(args):
                 "fp64_probe": {"gflops": peak_meas, "ms": peak_ms,
                                "what": "mrrr_probe_fp64_fma: 8 warps per SM, 8 independent DFMA chains per thread"},
                 "comparison": comparison,
-                "tree": {nm: last[0][key] for nm, key in
-                         (("d_max", "d_max"), ("clusters", "nclusters"), ("largest_cluster", "largest_cluster"),
-                          ("reps_failed", "reps_failed"), ("rqi_iters", "rqi_iters"), ("fallbacks", "fallbacks"))}}
+                "tree": _tree(last[0])}
         line["variants"] = _variants(m, mats, args, dev, flush)
         if not args.no_extras:
             for key, fn in (("c4_batched", lambda: _c4(m, dev, flush, args, peak_meas)),
@@ -479,6 +477,13 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _tree(st):
+    """Representation-tree statistics of one solve (Sec. 2 and 3.2)."""
+    keys = ("d_max", "nclusters", "largest_cluster", "reps_failed", "reps_relaxed", "reps_backtracked",
+            "rqi_iters", "fallbacks", "noconv")
+    return {k: st[k] for k in keys}
 
 
 def _compare(m, mats, step, args, dev, flush, value):
@@ -555,8 +560,7 @@ def _c4(m, dev, flush, args, peak_meas):
     acc = _sum_stats(sts)
     st = sts[-1][0]
     return {"value": pairs * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
-            "matrices": len(batch), "eigenpairs": pairs, "d_max": st["d_max"], "clusters": st["nclusters"],
-            "reps_failed": st["reps_failed"], "fallbacks": st["fallbacks"],
+            "matrices": len(batch), "eigenpairs": pairs, "tree": _tree(st),
             "roofline": _rqi_roofline(acc, pair_rows * k, "f64", peak_meas),
             "workload": "4096 tridiagonals, n log-uniform [32, 2048], seed 4, types uniform/1-2-1/Wilkinson/"
                         "glued W_21, fp32 in, fp64 internals, all pairs, one batched call per step"}
@@ -578,8 +582,7 @@ def _c3(m, dev, flush, args, peak_meas):
     st = sts[-1][0]
     n = int(d.size)
     return {"value": n * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k, "n": n,
-            "d_max": st["d_max"], "clusters": st["nclusters"], "largest_cluster": st["largest_cluster"],
-            "reps_failed": st["reps_failed"], "roofline": _rqi_roofline(acc, n * n * k, "dd", peak_meas),
+            "tree": _tree(st), "roofline": _rqi_roofline(acc, n * n * k, "dd", peak_meas),
             "workload": "glued Wilkinson 40 x W_201, couplings 1e-8, n=8040, fp64 in, double-double internals"}
 
 

@@ -178,6 +178,24 @@ int mrrr_solve_batch_d(int nb, const int* n, const double* const* d, const doubl
                        double* const* Z, const int* ldz, int* status, void* stream);
 
 /*
+ * Dense symmetric eigenproblem A z = lambda z (the dense experiment of
+ * Sec. 5, Fig. 3): Householder reduction of A to tridiagonal form
+ * T = Q^T A Q in the I/O precision, the tridiagonal solve of
+ * mrrr_solve_s / _d (mode MRRR_MIXED or MRRR_PLAIN, params, range as
+ * there), and back-transformation Z = Q Z_T.  A is n x n, column-major with
+ * leading dimension lda >= n, symmetric (both triangles are read, neither
+ * is written); W and Z as for mrrr_solve_s.  A, W, Z may be host or device
+ * pointers.  The reduction costs O(n^3) and dominates the time for large
+ * n; the tridiagonal stage sets the accuracy of the eigenvectors.  n is at
+ * most 46340.  Returns as mrrr_solve_s.
+ */
+int mrrr_syev_s(int n, const float* A, int lda, mrrr_range range, float vl, float vu, int il, int iu,
+                mrrr_mode mode, const mrrr_params* params, int* m_out, float* W, float* Z, int ldz, void* stream);
+int mrrr_syev_d(int n, const double* A, int lda, mrrr_range range, double vl, double vu, int il, int iu,
+                mrrr_mode mode, const mrrr_params* params, int* m_out, double* W, double* Z, int ldz,
+                void* stream);
+
+/*
  * Index partition for independent solves of one matrix, e.g. one part per
  * GPU (the eigenpairs of an index range need no data from the other
  * ranges).  Splits 1..n into nparts contiguous ranges il[p]..iu[p]

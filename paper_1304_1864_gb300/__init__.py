@@ -12,5 +12,5 @@ from ._binding import (  # noqa: F401
     mrrr_solve_batch_s, mrrr_solve_d, mrrr_solve_s, mrrr_strerror, mrrr_version, solve, solve_batch, strerror,
     MRRR_PENDING, MrrrRequest, MrrrServeConfig, MrrrServeInfo, MrrrServeStats, Server, mrrr_serve_close,
     mrrr_serve_open, mrrr_serve_poll, mrrr_serve_stats_get, mrrr_serve_submit, mrrr_probe_fp64_fma, probe_fp64,
-    mrrr_partition_s, mrrr_partition_d, partition,
+    mrrr_partition_s, mrrr_partition_d, partition, mrrr_syev_s, mrrr_syev_d, solve_dense,
 )

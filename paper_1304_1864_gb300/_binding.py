@@ -100,6 +100,12 @@ def lib():
             f.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_int, ctypes.POINTER(MrrrParams), vp,
                           vp, vp, vp, vp, vp]
             f.restype = ctypes.c_int
+        for name, real in (("mrrr_syev_s", ctypes.c_float), ("mrrr_syev_d", ctypes.c_double)):
+            f = getattr(L, name)
+            f.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, real, real, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_int, ctypes.POINTER(MrrrParams), ctypes.POINTER(ctypes.c_int), vp, vp, ctypes.c_int,
+                          vp]
+            f.restype = ctypes.c_int
         for name in ("mrrr_partition_s", "mrrr_partition_d"):
             f = getattr(L, name)
             f.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, ctypes.POINTER(MrrrParams), ctypes.c_int, vp, vp, vp]
@@ -149,6 +155,14 @@ def mrrr_solve_batch_s(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, stat
 
 def mrrr_solve_batch_d(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, status, stream):
     return lib().mrrr_solve_batch_d(nb, n, d, e, il, iu, mode, params, m_out, W, Z, ldz, status, stream)
+
+
+def mrrr_syev_s(n, A, lda, rng, vl, vu, il, iu, mode, params, m_out, W, Z, ldz, stream):
+    return lib().mrrr_syev_s(n, A, lda, rng, vl, vu, il, iu, mode, params, m_out, W, Z, ldz, stream)
+
+
+def mrrr_syev_d(n, A, lda, rng, vl, vu, il, iu, mode, params, m_out, W, Z, ldz, stream):
+    return lib().mrrr_syev_d(n, A, lda, rng, vl, vu, il, iu, mode, params, m_out, W, Z, ldz, stream)
 
 
 def mrrr_partition_s(n, d, e, mode, params, nparts, il, iu, stream):
@@ -318,6 +332,43 @@ def solve_batch(mats, mode="mixed", ranges=None, stream=None, timing=False, chec
         raise MrrrError(rc, "mrrr_solve_batch")
     out = [(Ws[i][:mout[i]], Zts[i][:mout[i]].T) for i in range(nb)]
     return out, stats.as_dict() | {"status": rc}, list(status)
+
+
+def solve_dense(A, mode="mixed", range="all", vl=0.0, vu=0.0, il=1, iu=None, stream=None, timing=False,
+                check=True, **param_kw):
+    """Eigenpairs of the dense symmetric matrix A (torch tensor or numpy
+    array, float32 -> mrrr_syev_s, float64 -> mrrr_syev_d).  A is read in
+    column-major order (for a symmetric matrix that is A itself).  Returns
+    (W, Z, stats) with Z of shape (n, m) on the same side as A."""
+    torch_in = _is_torch(A)
+    n = int(A.shape[0])
+    single = str(A.dtype).endswith("float32")
+    rng = {"all": MRRR_ALL, "index": MRRR_INDEX, "value": MRRR_VALUE}[range]
+    iu = n if iu is None else iu
+    k = (iu - il + 1) if rng == MRRR_INDEX else n
+    kk = max(k, 1)
+    if torch_in:
+        import torch
+        A = A.contiguous()
+        W = torch.empty(kk, dtype=A.dtype, device=A.device)
+        Zt = torch.empty((kk, max(n, 1)), dtype=A.dtype, device=A.device)
+        dev = A.is_cuda
+    else:
+        A = np.ascontiguousarray(A)
+        W = np.empty(kk, dtype=A.dtype)
+        Zt = np.empty((kk, max(n, 1)), dtype=A.dtype)
+        dev = False
+    stats = MrrrStats()
+    prm = make_params(stats=stats, flags=(MRRR_FLAG_TIMING if timing else 0) | param_kw.pop("flags", 0), **param_kw)
+    m = ctypes.c_int(0)
+    fn = mrrr_syev_s if single else mrrr_syev_d
+    real = ctypes.c_float if single else ctypes.c_double
+    rc = fn(n, _ptr(A), max(n, 1), rng, real(vl), real(vu), il, iu, MRRR_MIXED if mode == "mixed" else MRRR_PLAIN,
+            ctypes.byref(prm), ctypes.byref(m), _ptr(W), _ptr(Zt), max(n, 1), _stream_handle(stream, dev))
+    if check and rc not in (MRRR_OK, MRRR_ERR_NOCONV):
+        raise MrrrError(rc, "mrrr_syev_" + ("s" if single else "d"))
+    mm = m.value
+    return W[:mm], Zt[:mm].T, stats.as_dict() | {"status": rc}
 
 
 def partition(d, e, nparts, mode="mixed", stream=None, **param_kw):

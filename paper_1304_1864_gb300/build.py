@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmrrr.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["solver_s.cu", "solver_d.cu", "capi.cu", "noalloc.cu", "serve.cu", "probe.cu"]
+UNITS = ["solver_s.cu", "solver_d.cu", "capi.cu", "noalloc.cu", "serve.cu", "probe.cu", "dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INC, "-I" + CSRC]
 
