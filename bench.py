@@ -442,7 +442,12 @@ def run_ours(args):
     roofline["traffic_note"] = ("bytes per launch, mean of the launches of one ncu capture of this kernel on this "
                                 "workload" if roofline["traffic"] else "kernel changed since the last ncu capture")
     line = None
-    if rank == 0:
+    if rank == 0 and args.step_only:
+        # only the timed steps (for launch lists and counter captures)
+        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "step_only": True,
+                          "roofline": roofline, "gpu_launches": acc["launches"]}), flush=True)
+    elif rank == 0:
         _log("timed steps: %.1f ms" % ms_total)
         comparison = _compare(m, mats, step, args, dev, flush, value)
         _log("plain comparison done")
@@ -468,6 +473,7 @@ def run_ours(args):
         if not args.no_extras:
             for key, fn in (("c4_batched", lambda: _c4(m, dev, flush, args, peak_meas)),
                             ("c3_dd", lambda: _c3(m, dev, flush, args, peak_meas)),
+                            ("dense", lambda: _dense(m, dev, flush, args)),
                             ("serve", lambda: _serve(m, dev, args))):
                 t0 = time.perf_counter()
                 line[key] = fn()
@@ -584,6 +590,42 @@ def _c3(m, dev, flush, args, peak_meas):
     return {"value": n * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k, "n": n,
             "tree": _tree(st), "roofline": _rqi_roofline(acc, n * n * k, "dd", peak_meas),
             "workload": "glued Wilkinson 40 x W_201, couplings 1e-8, n=8040, fp64 in, double-double internals"}
+
+
+def _dense(m, dev, flush, args):
+    """The dense experiment of Sec. 5 (Fig. 3): A = Q T Q^T with T the n = 2000
+    1-2-1 matrix and Q the orthogonal factor of a seeded Gaussian matrix,
+    fp32 in/out; reduction to tridiagonal form, tridiagonal MRRR (mixed, and
+    plain for comparison), back-transformation, all eigenpairs, one
+    mrrr_syev_s call per step.  Residual ||A z - w z||_2 / (||A||_1 n eps) and
+    orthogonality in units of n eps, evaluated on the device in binary64."""
+    import torch
+    from paper_1304_1864_gb300 import inputs
+    n = 2000
+    d, e = inputs.one_two_one(n)
+    rng = np.random.default_rng(7)
+    Q, R = np.linalg.qr(rng.standard_normal((n, n)))
+    Q *= np.sign(np.diag(R))
+    A = Q @ (np.diag(d) + np.diag(e, 1) + np.diag(e, -1)) @ Q.T
+    Ag = torch.tensor(0.5 * (A + A.T), dtype=torch.float32, device=dev)
+    out = {"n": n, "workload": "A = Q T Q^T, T = 1-2-1 (n = 2000), Q from a seeded Gaussian matrix, fp32 in/out, "
+                               "all eigenpairs, one mrrr_syev_s call per step"}
+    for mode in ("mixed", "plain"):
+        m.solve_dense(Ag, mode=mode)
+        torch.cuda.synchronize(dev)
+        k = max(1, min(args.extra_steps, 3))
+        ms, sts = _time_steps(lambda: [m.solve_dense(Ag, mode=mode)], k, dev, flush)
+        W, Z, st = sts[-1][0]
+        A64, Z64, W64 = Ag.double(), Z.double(), W.double()
+        R = A64 @ Z64 - Z64 * W64[None, :]
+        an = float(A64.abs().sum(dim=0).max())
+        eps = 2.0 ** -24
+        G = Z64.T @ Z64
+        G.diagonal().sub_(1.0)
+        out[mode] = {"value": n * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+                     "residual_neps": float(R.norm(dim=0).max()) / (an * n * eps),
+                     "orthogonality_neps": float(G.abs().max()) / (n * eps)}
+    return out
 
 
 def _serve_run(m, dev, trace):
@@ -729,6 +771,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, C3, C4 and serving measurements")
+    ap.add_argument("--step-only", action="store_true",
+                    help="only the warm-up and timed steps of the headline workload (for profiling)")
     ap.add_argument("--extra-steps", type=int, default=10, help="timed steps of the C3 and C4 legs")
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[2.0, 5.0, 10.0, 20.0],
                     help="offered Poisson rates (requests/s) of the serving sweep")

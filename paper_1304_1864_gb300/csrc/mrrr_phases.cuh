@@ -152,8 +152,23 @@ MRRR_HD double root_candidate(const BlockDesc& B, const double* wd, const double
         double mu = side ? gu + delta : gl - delta;
         double g;
 #if defined(__CUDA_ARCH__)
-        if constexpr (std::is_same<Y, double>::value) g = ldl_factor_fast(wd + B.row0, we + B.row0, n, mu, side ? -1 : +1, rep);
-        else
+        if constexpr (std::is_same<Y, double>::value) {
+            g = ldl_factor_fast(wd + B.row0, we + B.row0, n, mu, side ? -1 : +1, rep);
+        } else if constexpr (std::is_same<Y, dd>::value) {
+            // double-double root: the factorization in binary64, widened
+            // exactly.  The random relative perturbation of size xi = 4 eps_x
+            // that follows (root_element) is as large as the rounding of a
+            // binary64 factorization, so the root is still T - mu I perturbed
+            // element-wise by O(eps_x) -- at the latency of binary64 instead of
+            // a serial chain of double-double divisions.  The factorization is
+            // written as binary64 into the first 2n words of this side's
+            // region and widened in place from the top down (double-double
+            // entry i covers binary64 words 2i, 2i+1 >= i).
+            double* tmp = (double*)rep;
+            g = ldl_factor_fast(wd + B.row0, we + B.row0, n, mu, side ? -1 : +1, tmp);
+            if (g < INFINITY)
+                for (int i = 2 * n - 1; i >= 0; --i) rep[i] = dd(tmp[i]);
+        } else
 #endif
             g = ldl_factor<Y>(wd + B.row0, we + B.row0, n, mu, side ? -1 : +1, rep);
         if (g < INFINITY) {
