@@ -14,7 +14,8 @@
 //     p = tau A22 v,  w = p - (tau / 2)(p^T v) v,  A22 -= v w^T + w v^T.
 // Then d_k = A[k, k], e_k = beta.  The eigenvectors of A are Q z with
 // Q = H_0 H_1 ... H_{n-3}, applied to the tridiagonal eigenvectors in reverse
-// order: Z[k+1:n, :] -= tau_k v_k (v_k^T Z[k+1:n, :]).
+// order: Z[k+1:n, :] -= tau_k v_k (v_k^T Z[k+1:n, :]); each column is then
+// signed so that its entry of largest magnitude is positive.
 //
 // Reductions (norms, the columns of A22 v, the dot products of the
 // back-transformation) are fixed-order trees in x, so a result does not
@@ -193,6 +194,43 @@ __global__ void k_ger(const X* A, int n, int k, const X* tau, X* Z, int ldz, con
     Z[(size_t)j * ldz + (k + 1) + i] -= tau[k] * vi * s[j];
 }
 
+// Sign convention of the back-transformed vectors (one CTA per column): the
+// entry of largest magnitude (the first on ties) is made positive.
+template <class X>
+__global__ void k_sign(X* Z, int n, int ldz) {
+    __shared__ X sv[kT];
+    __shared__ int si[kT];
+    X* z = Z + (size_t)blockIdx.x * ldz;
+    X best = -1;
+    int bi = 0;
+    for (int i = threadIdx.x; i < n; i += kT) {
+        const X a = fabs(z[i]);
+        if (a > best) {
+            best = a;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int h = kT / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            const X b = sv[threadIdx.x + h];
+            const int j = si[threadIdx.x + h];
+            if (b > sv[threadIdx.x] || (b == sv[threadIdx.x] && j < si[threadIdx.x])) {
+                sv[threadIdx.x] = b;
+                si[threadIdx.x] = j;
+            }
+        }
+        __syncthreads();
+    }
+    __shared__ int flip;
+    if (threadIdx.x == 0) flip = z[si[0]] < 0;
+    __syncthreads();
+    if (flip)
+        for (int i = threadIdx.x; i < n; i += kT) z[i] = -z[i];
+}
+
 struct Buf {
     void* p = nullptr;
     cudaStream_t st;
@@ -271,6 +309,7 @@ int syev_one(int n, const X* A, int lda, mrrr_range range, X vl, X vu, int il, i
             k_dotv<X><<<mfound, kT, 0, st>>>(Aw, n, k, Zt, n, s);
             k_ger<X><<<dim3(grid1(m), mfound), kT, 0, st>>>(Aw, n, k, tau, Zt, n, s);
         }
+        k_sign<X><<<mfound, kT, 0, st>>>(Zt, n, n);
         if (cudaGetLastError() != cudaSuccess) return MRRR_ERR_CUDA;
         const cudaMemcpyKind kW = kw == mrrr::PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
         const cudaMemcpyKind kZ = kz == mrrr::PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

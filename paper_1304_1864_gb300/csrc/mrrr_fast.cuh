@@ -148,6 +148,58 @@ __device__ __forceinline__ int negcount_fast(const double* __restrict__ D, const
     return cnt;
 }
 
+// Guarded double-double count (out of line) for the projective one's
+// fallback.
+static __device__ __noinline__ int negcount_dd_guarded(const dd* D, const dd* LLD, int n, dd tau, dd pivmin) {
+    return negcount<dd>(D, LLD, n, tau, pivmin);
+}
+
+// The double-double Sturm count in the projective form of negcount_fast:
+//     P_i = d_i P_{i-1} + N_i,   N_{i+1} = lld_i N_i - tau P_i,
+// a pivot negative where P changes sign.  Each row is three double-double
+// products and two sums (about 60 binary64 instructions) instead of a sum, a
+// product and a double-double division (about 140): the division alone is
+// three binary64 divisions and three double-double sums.  Every operation is
+// rounded once in double-double, so the count is exact for the
+// representation perturbed element-wise by a few units of 2^-104 -- the mixed
+// relative stability of Sec. 2.  The pair is rescaled every sixteen rows by
+// the power of two that brings the high word of P into [1, 2); an overflow,
+// or a P that is zero or subnormal at a rescaling point or at the end, sends
+// the count to the guarded divide form.
+__device__ __forceinline__ int negcount_dd_fast(const dd* __restrict__ D, const dd* __restrict__ LLD, int n, dd tau,
+                                                dd pivmin) {
+    const dd mtau = -tau;
+    dd P(1.0), N = mtau;
+    unsigned hp = 0u;  // high word of P_{i-1}.hi
+    int cnt = 0;
+    unsigned bad = 0u;
+    auto row = [&](int i) {
+        const dd a = LLD[i] * N;
+        P = D[i] * P + N;
+        const unsigned h = (unsigned)__double2hiint(P.hi);
+        cnt += (int)((h ^ hp) >> 31);
+        hp = h;
+        N = a + mtau * P;
+    };
+    int i = 0;
+    for (; i + 16 <= n - 1; i += 16) {  // sixteen rows, then the rescale
+        const int ip = min(i + kPrefetch, n - 1);
+        pf_l2(D + ip);
+        pf_l2(LLD + ip);
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) row(i + k);
+        bad |= dnotnormal(P.hi);
+        const double f = dpow2(dscale_exp(P.hi));
+        P = dd(P.hi * f, P.lo * f);
+        N = dd(N.hi * f, N.lo * f);
+    }
+    for (; i < n - 1; ++i) row(i);
+    P = D[n - 1] * P + N;
+    cnt += (int)((((unsigned)__double2hiint(P.hi)) ^ hp) >> 31);
+    if (bad | dnotnormal(P.hi) | !dfinite(N.hi)) return negcount_dd_guarded(D, LLD, n, tau, pivmin);
+    return cnt;
+}
+
 // The low-precision Sturm count of the pre-bisection (binary32 under a
 // binary64 working precision, see negcount_lo) in the same projective form
 // as negcount_fast: two dependent FMAs per row instead of an add, a divide
@@ -594,6 +646,113 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
     res.neg = neg;
     res.nrm2 = nrm2;
     *gamma = gam;
+    return res;
+}
+
+// Guarded generic double-double twisted solve (out of line) at a given twist
+// index, with the arg-max of |z| (the projective step's fallback).
+static __device__ __noinline__ TwistResult<dd> twisted_dd_guarded(const dd* rep, int n, dd lam, dd pivmin,
+                                                                 const Scratch<dd>& W, dd* gamma, int r, int* imax) {
+    return twisted_solve<dd>(rep, n, lam, pivmin, W, gamma, r, imax);
+}
+
+// The fixed-r twisted step of twisted_fixed_proj in double-double: the same
+// projective walk (X' = a X + Y, Y' = b Y - lam X', r stationary rows
+// top-down, then the progressive rows bottom-up) and the same telescoped
+// solve (z_i = w_i P_{i-1}, w_i = -ld_i w_{i+1}; below r with R_{i+1}), with
+// no division per row: a row of the walk is three double-double products
+// and two sums (about 60 binary64 instructions) against a double-double
+// division, a sum and two products (about 150) in the generic step.  gamma_r
+// = N_r / P_{r-1} + Q_r / R_{r+1} + lam takes the step's only two divisions.
+// X is rescaled by a power of two where it leaves [2^-256, 2^256), right
+// after it was stored, and the solve multiplies its running factor by the
+// same power where it meets that stored value.  An overflow, or a vanished
+// pivot at the twist, sends the step to the generic solve.
+__device__ __forceinline__ TwistResult<dd> twisted_fixed_proj_dd(const dd* __restrict__ rep, int n, dd lam,
+                                                                dd pivmin, const Scratch<dd>& W, dd* gamma,
+                                                                int* imax, int r) {
+    const dd* __restrict__ D = rep;
+    const dd* __restrict__ LD = rep + 2 * n;
+    const dd* __restrict__ LLD = rep + 3 * n;
+    dd* __restrict__ A = W.a;
+    const dd mlam = -lam;
+    const int steps = n - 1;
+    int neg = 0;
+    auto wrow = [&](int k) { return k < r ? k : n - 2 - (k - r); };
+    const dd ylast = D[n - 1] - lam;
+    dd X(1.0), Y = r > 0 ? mlam : ylast;
+    dd Xtop(1.0), Ytop = mlam;
+    unsigned hx = (unsigned)__double2hiint(X.hi);
+    for (int k = 0; k < steps; ++k) {
+        if ((k & 15) == 0) {
+            const int ip = wrow(min(k + kPrefetch, steps - 1));
+            pf_l2(D + ip);
+            pf_l2(LLD + ip);
+        }
+        const bool st = k < r;
+        const int i = wrow(k);
+        const dd a = st ? D[i] : LLD[i];
+        const dd b = st ? LLD[i] : D[i];
+        A[st ? i : i + 1] = X;
+        if (dneeds_rescale(X.hi)) {
+            const double f = dpow2(dscale_exp(X.hi));
+            X = dd(X.hi * f, X.lo * f);
+            Y = dd(Y.hi * f, Y.lo * f);
+        }
+        const dd t = b * Y;
+        X = a * X + Y;
+        const unsigned h = (unsigned)__double2hiint(X.hi);
+        neg += (int)((h ^ hx) >> 31);
+        hx = h;
+        Y = t + mlam * X;
+        if (k + 1 == r) {  // the stationary rows are done: the progressive chain starts
+            Xtop = X;
+            Ytop = Y;
+            X = dd(1.0);
+            Y = ylast;
+            hx = (unsigned)__double2hiint(X.hi);
+        }
+    }
+    const dd gam = Ytop / Xtop + Y / X + lam;
+    neg += dsign(gam.hi);
+    if (dnotnormal(Xtop.hi) | dnotnormal(X.hi) | !dfinite(gam.hi))
+        return twisted_dd_guarded(rep, n, lam, pivmin, W, gamma, r, imax);
+    // solve: z_r = 1, then from r outwards (down, then up)
+    A[r] = dd(1.0);
+    dd nrm2(1.0);
+    unsigned long long zmax = dabsbits(1.0);
+    int im = r;
+    auto sstep = [&](dd& f, int iz, int il) {
+        const dd av = A[iz];
+        f = -(LD[il] * f);
+        if (dneeds_rescale(av.hi)) {
+            const double g = dpow2(dscale_exp(av.hi));
+            f = dd(f.hi * g, f.lo * g);
+        }
+        const dd z = f * av;
+        A[iz] = z;
+        nrm2 = nrm2 + z * z;
+        const unsigned long long za = dabsbits(z.hi);
+        const bool better = za > zmax;
+        zmax = better ? za : zmax;
+        im = better ? iz : im;
+    };
+    dd f = dd(1.0) / Xtop;  // w_r
+    for (int iz = r - 1; iz >= 0; --iz) {
+        if (((r - 1 - iz) & 15) == 0) pf_l2(A + max(iz - kPrefetch, 0));
+        sstep(f, iz, iz);
+    }
+    f = dd(1.0) / X;  // v_r
+    for (int iz = r + 1; iz < n; ++iz) {
+        if (((iz - r - 1) & 15) == 0) pf_l2(A + min(iz + kPrefetch, n - 1));
+        sstep(f, iz, iz - 1);
+    }
+    *imax = im;
+    *gamma = gam;
+    TwistResult<dd> res;
+    res.r = r;
+    res.neg = neg;
+    res.nrm2 = nrm2;
     return res;
 }
 

@@ -363,12 +363,14 @@ MRRR_HD double babs(double x) { return fabs(x); }
 MRRR_HD dd babs(const dd& x) { return dd_abs(x); }
 MRRR_HD float babs(float x) { return fabsf(x); }
 
-// Sturm count for bisection: the tuned binary64 count on the device when
-// FAST (classification brackets), the fully accurate one otherwise.
+// Sturm count for bisection: the tuned projective counts on the device when
+// FAST (binary64 and double-double; classification brackets and their
+// verification), the guarded divide form otherwise.
 template <class Y, bool FAST>
 MRRR_HD int count_at(const Y* D, const Y* LLD, int n, Y tau, Y pm) {
 #if defined(__CUDA_ARCH__)
     if constexpr (FAST && std::is_same<Y, double>::value) return negcount_fast(D, LLD, n, tau, pm);
+    if constexpr (FAST && std::is_same<Y, dd>::value) return negcount_dd_fast(D, LLD, n, tau, pm);
 #endif
     return negcount<Y>(D, LLD, n, tau, pm);
 }
@@ -929,9 +931,14 @@ MRRR_HD TwistResult<Y> twist_step(const Y* rep, int n, Y lam, Y pm, const Scratc
         if (Wk.stride == 1) return twisted_solve_fast(rep, n, lam, to_d(pm), Wk.a, Wk.b, gamma, imax, r_hint);
     }
 #endif
-    // double-double, and the host build of binary64 (which follows the
-    // device's steps): the generic solve, at the given twist index when
-    // there is one
+#if defined(__CUDA_ARCH__)
+    if constexpr (std::is_same<Y, dd>::value) {
+        if (Wk.stride == 1 && r_hint >= 0) return twisted_fixed_proj_dd(rep, n, lam, pm, Wk, gamma, imax, r_hint);
+    }
+#endif
+    // double-double without a twist index, and the host build of binary64
+    // (which follows the device's steps): the generic solve, at the given
+    // twist index when there is one
     if constexpr (std::is_same<Y, dd>::value || std::is_same<Y, double>::value)
         return twisted_solve<Y>(rep, n, lam, pm, Wk, gamma, r_hint, imax);
     *imax = -1;
