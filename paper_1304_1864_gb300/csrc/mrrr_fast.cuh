@@ -78,6 +78,29 @@ __device__ __forceinline__ bool dneeds_rescale(double x) {
     const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
     return e != 0u && e - (1023u - 256u) >= 512u;
 }
+
+// x 2^k by integer arithmetic on the exponent field, so that a rescale
+// costs no FP64 issue slot.  On this GPU an FP64 multiply under a false
+// predicate holds the FP64 pipe as long as an executed one, and the
+// per-row rescale tests of the twisted walk and solve are if-converted: a
+// multiply there would cost every row a slot.  Exact wherever x 2^k is a
+// normal number; a zero or subnormal x, or a result below the normal range,
+// becomes a zero of the same sign (the projective values it scales are then
+// negligible next to the ones kept), a result above it becomes an infinity
+// (which the callers' final finiteness checks catch), and an infinity or
+// NaN stays as it is.
+__device__ __forceinline__ double dscale_bits(double x, int k) {
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const int en = e + k;
+    const unsigned sgn = hi & 0x80000000u;
+    const bool keep = e == 0x7ff;
+    const bool zero = !keep && (e == 0 || en <= 0);
+    const bool inf = !keep && !zero && en >= 0x7ff;
+    const unsigned nhi = keep ? hi : zero ? sgn : inf ? (sgn | 0x7ff00000u) : hi + ((unsigned)k << 20);
+    const int nlo = (keep || !(zero || inf)) ? __double2loint(x) : 0;
+    return __hiloint2double((int)nhi, nlo);
+}
 // Sturm count (number of eigenvalues of L D L^T below tau) for bisection and
 // bracket checks, without a divide.  The stationary transform maps s_i to
 // s_{i+1} = lld_i s_i / (d_i + s_i) - tau, a linear fractional map; writing
@@ -264,6 +287,101 @@ __device__ __forceinline__ int negcount_lo_fast(const float* __restrict__ D, con
     if (bad | (unsigned)(ee == 0u || ee == 255u) | (unsigned)!isfinite(N))
         return negcount_lo_guarded(D, LLD, n, tau, pivmin);
     return cnt;
+}
+
+// First twist index of an RQI step from the binary32 copy of the rep
+// (Sec. 2, "Rayleigh quotient iteration": r = argmin_k |gamma_k| with
+// gamma_k = s_k + p_k + tau, from the stationary and the progressive
+// transform at tau), in projective form: s_i = N_i / P_{i-1} as in
+// negcount_lo_fast, and p_i = Q_i / R_{i+1} with R_n = 1,
+// Q_{n-1} = d_{n-1} - tau,
+//     R_{i+1} = lld_i R_{i+2} + Q_{i+1}     (= R_{i+2} (lld_i + p_{i+1}))
+//     Q_i     = d_i Q_{i+1} - tau R_{i+1}   (so p_i = d_i p_{i+1} / (lld_i + p_{i+1}) - tau).
+// A row's dependency chain is two FMAs; the ratios come from approximate
+// reciprocals off the chain (only the position of the smallest |gamma_k|
+// matters).  Both pairs are rescaled by a power of two every four rows.
+// s_k is kept in s_store for the bottom-up pass.  Returns r (smallest index
+// on ties), or -1 when a rescaling point met a zero, subnormal or
+// non-finite value, or no gamma_k is finite (the caller then factors in the
+// working precision).
+__device__ __forceinline__ int twist_index_lo_fast(const float* __restrict__ D, const float* __restrict__ LLD,
+                                                   int n, float tau, float* __restrict__ s_store) {
+    const float mtau = -tau;
+    unsigned bad = 0u;
+    auto rescale = [&](float& u, float& v) {
+        const int e = (int)((__float_as_uint(u) >> 23) & 0xffu);
+        bad |= (unsigned)(e == 0 || e == 255);
+        const float f = __uint_as_float((unsigned)(max(127 - e, -126) + 127) << 23);
+        u *= f;
+        v *= f;
+    };
+    // stationary, top-down
+    float P = 1.0f, N = mtau;
+    int i = 0;
+    for (; i + 8 <= n - 1; i += 8) {
+        const int ip = min(i + kPrefetch, n - 1);
+        pf_l2(D + ip);
+        pf_l2(LLD + ip);
+        float d[8], l[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            d[k] = __ldg(D + i + k);
+            l[k] = __ldg(LLD + i + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            s_store[i + k] = __fdividef(N, P);
+            const float a = l[k] * N;
+            P = fmaf(d[k], P, N);
+            N = fmaf(mtau, P, a);
+            if ((k & 3) == 3) rescale(P, N);
+        }
+    }
+    for (; i < n - 1; ++i) {
+        s_store[i] = __fdividef(N, P);
+        const float a = __ldg(LLD + i) * N;
+        P = fmaf(__ldg(D + i), P, N);
+        N = fmaf(mtau, P, a);
+    }
+    rescale(P, N);
+    const float s_last = __fdividef(N, P);
+    // progressive, bottom-up, with the running arg-min of |gamma_k|
+    float R = 1.0f, Q = __ldg(D + n - 1) - tau;
+    float gbest = s_last + Q + tau;
+    int r = n - 1;
+    auto row = [&](int j, float dj, float lj, float sj) {
+        const float t = dj * Q;
+        R = fmaf(lj, R, Q);
+        Q = fmaf(mtau, R, t);
+        const float g = sj + __fdividef(Q, R) + tau;
+        if (fabsf(g) <= fabsf(gbest)) {  // smallest index on ties (the walk goes down)
+            gbest = g;
+            r = j;
+        }
+    };
+    i = n - 2;
+    for (; i - 7 >= 0; i -= 8) {
+        const int ip = max(i - kPrefetch, 0);
+        pf_l2(D + ip);
+        pf_l2(LLD + ip);
+        pf_l2(s_store + ip);
+        float d[8], l[8], sv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            d[k] = __ldg(D + i - k);
+            l[k] = __ldg(LLD + i - k);
+            sv[k] = s_store[i - k];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            row(i - k, d[k], l[k], sv[k]);
+            if ((k & 3) == 3) rescale(R, Q);
+        }
+    }
+    for (; i >= 0; --i) row(i, __ldg(D + i), __ldg(LLD + i), s_store[i]);
+    rescale(R, Q);
+    if (bad || !isfinite(gbest)) return -1;
+    return r;
 }
 
 // Pre-bisection count for the low precision Lo of the device path
@@ -495,11 +613,12 @@ constexpr int kGp = 4;
 // from the neighbouring multipliers), and the underflowed tail of a
 // localized vector stays zero.
 //
-// Where X leaves [2^-512, 2^512), X and Y are scaled by the power of two 2^k
+// Where X leaves [2^-256, 2^256), X and Y are scaled by the power of two 2^k
 // that brings X into [1, 2) -- the ratios and the signs do not change --
 // right after X was stored, so that both the decision and k follow from the
 // stored value itself; the solve, reaching that entry, multiplies its
-// running factor by 2^k.  An overflow, or a vanished pivot at the twist
+// running factor by 2^k.  Both scalings work on the exponent fields
+// (dscale_bits), with no FP64 instruction.  An overflow, or a vanished pivot at the twist
 // (P_{r-1} or R_{r+1} zero), sends the step to the guarded generic solve.
 __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* __restrict__ rep, int n, double lam,
                                                                  double pivmin, double* __restrict__ A,
@@ -526,9 +645,9 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
         const int i = wrow(k);
         A[st ? i : i + 1] = X;
         if (dneeds_rescale(X)) {
-            const double f = dpow2(dscale_exp(X));
-            X *= f;
-            Y *= f;
+            const int q = dscale_exp(X);
+            X = dscale_bits(X, q);
+            Y = dscale_bits(Y, q);
         }
         const double t = b * Y;
         X = fma(a, X, Y);
@@ -601,7 +720,7 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
         const int iz = sz(k);
         if (k == r) f = vr;  // the upward walk restarts at v_r
         f = -(l * f);
-        if (dneeds_rescale(a)) f *= dpow2(dscale_exp(a));
+        if (dneeds_rescale(a)) f = dscale_bits(f, dscale_exp(a));
         const double z = f * a;
         A[iz] = z;
         nrm2 = fma(z, z, nrm2);
@@ -695,9 +814,9 @@ __device__ __forceinline__ TwistResult<dd> twisted_fixed_proj_dd(const dd* __res
         const dd b = st ? LLD[i] : D[i];
         A[st ? i : i + 1] = X;
         if (dneeds_rescale(X.hi)) {
-            const double f = dpow2(dscale_exp(X.hi));
-            X = dd(X.hi * f, X.lo * f);
-            Y = dd(Y.hi * f, Y.lo * f);
+            const int q = dscale_exp(X.hi);
+            X = dd(dscale_bits(X.hi, q), dscale_bits(X.lo, q));
+            Y = dd(dscale_bits(Y.hi, q), dscale_bits(Y.lo, q));
         }
         const dd t = b * Y;
         X = a * X + Y;
@@ -726,8 +845,8 @@ __device__ __forceinline__ TwistResult<dd> twisted_fixed_proj_dd(const dd* __res
         const dd av = A[iz];
         f = -(LD[il] * f);
         if (dneeds_rescale(av.hi)) {
-            const double g = dpow2(dscale_exp(av.hi));
-            f = dd(f.hi * g, f.lo * g);
+            const int q = dscale_exp(av.hi);
+            f = dd(dscale_bits(f.hi, q), dscale_bits(f.lo, q));
         }
         const dd z = f * av;
         A[iz] = z;

@@ -1032,7 +1032,12 @@ MRRR_HD bool rqi_item(Item& I, MatrixDesc* mats, const BlockDesc* blocks, const 
             I.rep_lo != nullptr) {
             typedef typename LowType<Y>::T Lo;
             const Lo* Dl = (const Lo*)I.rep_lo;
-            r_hint = twist_index_lo<Lo>(Dl, Dl + n, n, (Lo)to_d(lam), (Lo*)Wk.a);
+#if defined(__CUDA_ARCH__)
+            if constexpr (std::is_same<Lo, float>::value)
+                r_hint = twist_index_lo_fast(Dl, Dl + n, n, (float)to_d(lam), (float*)Wk.a);
+            else
+#endif
+                r_hint = twist_index_lo<Lo>(Dl, Dl + n, n, (Lo)to_d(lam), (Lo*)Wk.a);
             steps_low = 2ULL * n;
         }
         const int done0 = I.rqi_done;

@@ -531,6 +531,8 @@ __global__ void k_rqi(Item* items, const int* list, int count, const int* dev_to
                       int final_pass, int* park_list, int* park_count) {
     constexpr bool kCoop = !std::is_same<Y, dd>::value;
     __shared__ X tile[32][33];
+    __shared__ X* col_of[32];
+    __shared__ int rows_of[32];
     const int lane = threadIdx.x & 31;
     // this warp's scratch slot (one-warp CTAs), reused for every chunk it takes
     Y* base = scratch + ((size_t)blockIdx.x * 32 + lane) * (size_t)(2 * nmax);
@@ -572,23 +574,29 @@ __global__ void k_rqi(Item* items, const int* list, int count, const int* dev_to
             }
             int nmaxw = nrow;
             for (int o = 16; o > 0; o >>= 1) nmaxw = max(nmaxw, __shfl_xor_sync(0xffffffffu, nmaxw, o));
+            // every lane's column and length, read back by the whole warp
+            col_of[lane] = col;
+            rows_of[lane] = nrow;
+            __syncwarp();
             for (int r0 = 0; r0 < nmaxw; r0 += 32) {
                 // lane l: rows r0..r0+31 of its own vector into tile row l
-#pragma unroll 4
-                for (int q = 0; q < 32; ++q) {
-                    int r = r0 + q;
-                    tile[lane][q] = (r < nrow) ? (X)(to_d(Wk.a[r]) * scale) : X(0);
-                }
+                // (all 32 loads issued before the first use)
+                double v[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = (r0 + q < nrow) ? to_d(Wk.a[r0 + q]) : 0.0;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) tile[lane][q] = (X)(v[q] * scale);
                 __syncwarp();
                 // column c of the tile: lanes write 32 consecutive rows
+#pragma unroll 8
                 for (int c = 0; c < 32; ++c) {
-                    X* cc = (X*)__shfl_sync(0xffffffffu, (unsigned long long)col, c);
-                    int nc = __shfl_sync(0xffffffffu, nrow, c);
-                    int r = r0 + lane;
-                    if (cc && r < nc) cc[r] = tile[c][lane];
+                    X* cc = col_of[c];
+                    const int r = r0 + lane;
+                    if (cc && r < rows_of[c]) cc[r] = tile[c][lane];
                 }
                 __syncwarp();
             }
+            __syncwarp();
         }
     }
 }
