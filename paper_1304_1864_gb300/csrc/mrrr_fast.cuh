@@ -89,6 +89,14 @@ __device__ __forceinline__ bool dneeds_rescale(double x) {
 // negligible next to the ones kept), a result above it becomes an infinity
 // (which the callers' final finiteness checks catch), and an infinity or
 // NaN stays as it is.
+// x = m 2^e with |m| in [1, 2): returns m (x's exponent field set to that of
+// 1) and e, for a normal x, by integer arithmetic.
+__device__ __forceinline__ double dsplit_exp(double x, int& e) {
+    const unsigned hi = (unsigned)__double2hiint(x);
+    e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    return __hiloint2double((int)((hi & 0x800fffffu) | 0x3ff00000u), __double2loint(x));
+}
+
 __device__ __forceinline__ double dscale_bits(double x, int k) {
     const unsigned hi = (unsigned)__double2hiint(x);
     const int e = (int)((hi >> 20) & 0x7ffu);
@@ -714,14 +722,25 @@ __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* 
     double nrm2 = 1.0;
     unsigned long long zmax = dabsbits(1.0);
     int im = r;
-    double f = 1.0 / Xtop;  // w_r
-    const double vr = 1.0 / X;
+    // the running factor is f 2^fe with |f| in [1, 2): it can fall below the
+    // normal range between two far-apart peaks of the vector and rise again,
+    // so it is kept as a mantissa and an integer exponent, which also makes
+    // the walk's rescalings (2^q at the rows where the stored multiplier
+    // left the window) integer additions; only z itself is rounded into
+    // binary64 (an entry below the normal range becomes zero)
+    int fe, vre;
+    double f = dsplit_exp(1.0 / Xtop, fe);  // w_r
+    const double vr = dsplit_exp(1.0 / X, vre);
     auto sstep = [&](int k, double a, double l) {
         const int iz = sz(k);
-        if (k == r) f = vr;  // the upward walk restarts at v_r
-        f = -(l * f);
-        if (dneeds_rescale(a)) f = dscale_bits(f, dscale_exp(a));
-        const double z = f * a;
+        if (k == r) {  // the upward walk restarts at v_r
+            f = vr;
+            fe = vre;
+        }
+        int e;
+        f = dsplit_exp(-(l * f), e);
+        fe += e + (dneeds_rescale(a) ? dscale_exp(a) : 0);
+        const double z = dscale_bits(f * a, fe);
         A[iz] = z;
         nrm2 = fma(z, z, nrm2);
         const unsigned long long za = dabsbits(z);
@@ -841,14 +860,24 @@ __device__ __forceinline__ TwistResult<dd> twisted_fixed_proj_dd(const dd* __res
     dd nrm2(1.0);
     unsigned long long zmax = dabsbits(1.0);
     int im = r;
+    // the running factor is f 2^fe with |f.hi| in [1, 2), as in the binary64
+    // step: it neither underflows between far-apart peaks nor needs an FP64
+    // instruction to rescale
+    auto split = [](dd& f, int& fe) {
+        int e;
+        const double h = dsplit_exp(f.hi, e);
+        f = dd(h, dscale_bits(f.lo, -e));
+        fe = e;
+    };
+    int fe = 0;
     auto sstep = [&](dd& f, int iz, int il) {
         const dd av = A[iz];
         f = -(LD[il] * f);
-        if (dneeds_rescale(av.hi)) {
-            const int q = dscale_exp(av.hi);
-            f = dd(dscale_bits(f.hi, q), dscale_bits(f.lo, q));
-        }
-        const dd z = f * av;
+        int e;
+        split(f, e);
+        fe += e + (dneeds_rescale(av.hi) ? dscale_exp(av.hi) : 0);
+        const dd zm = f * av;
+        const dd z = dd(dscale_bits(zm.hi, fe), dscale_bits(zm.lo, fe));
         A[iz] = z;
         nrm2 = nrm2 + z * z;
         const unsigned long long za = dabsbits(z.hi);
@@ -857,11 +886,13 @@ __device__ __forceinline__ TwistResult<dd> twisted_fixed_proj_dd(const dd* __res
         im = better ? iz : im;
     };
     dd f = dd(1.0) / Xtop;  // w_r
+    split(f, fe);
     for (int iz = r - 1; iz >= 0; --iz) {
         if (((r - 1 - iz) & 15) == 0) pf_l2(A + max(iz - kPrefetch, 0));
         sstep(f, iz, iz);
     }
     f = dd(1.0) / X;  // v_r
+    split(f, fe);
     for (int iz = r + 1; iz < n; ++iz) {
         if (((iz - r - 1) & 15) == 0) pf_l2(A + min(iz + kPrefetch, n - 1));
         sstep(f, iz, iz - 1);

@@ -194,27 +194,27 @@ def test_variant_paths_n4001(flag):
             assert st["reps_failed"] == 0
 
 
-@pytest.mark.parametrize("prec,mode", [("d", "plain"), ("s", "mixed")])
-def test_backtracking_forced_by_the_test_hook(prec, mode):
+@pytest.mark.parametrize("prec,mode,coupling,gaptol", [("d", "plain", 1e-8, 0.0), ("s", "mixed", 1e-5, 1e-3)])
+def test_backtracking_forced_by_the_test_hook(prec, mode, coupling, gaptol):
     # twelve W_21 blocks glued together have clusters inside clusters: the
     # top eigenvalues of the copies form three groups, each of nearly equal
     # eigenvalues (gaps of a few units of 1e-15), about 0.6 x coupling apart.
-    # The groups must fall into one cluster at the root and stay unsplit:
-    # coupling 1e-8 for binary64 input (gaptol 1e-3); 2e-6 for binary32, below
-    # gaptol 1e-5 times the root shift's distance (about 0.25) and above the
-    # binary32 split threshold eps_x ||T||_1 (about 7e-7).  A group is then a
-    # cluster again in the child made for the whole set (d_max >= 2).  The
-    # test hook turns down every child representation built from a child, so
-    # each such cluster must be processed again with another shift one level
-    # up (backtracking, Sec. 3.2, "The representation tree"); the results
-    # still meet the targets of the mode and every eigenvalue matches the
-    # oracle.
+    # With gaptol 1e-3 (the plain binary64 default; set through the
+    # parameter block for the binary32/binary64 solver, whose default 1e-5
+    # resolves these groups in one level) the groups fall into one cluster at
+    # the root and each group is a cluster again in the child made for the
+    # whole set (d_max >= 2).  The test hook turns down every child
+    # representation built from a child, so each such cluster must be
+    # processed again with another shift one level up (backtracking, Sec.
+    # 3.2, "The representation tree"); the results still meet the targets of
+    # the mode and every eigenvalue matches the oracle.
     import paper_1304_1864_gb300 as m
-    d, e = inputs.glued_wilkinson(12, 21, 1e-8 if prec == "d" else 2e-6)
+    d, e = inputs.glued_wilkinson(12, 21, coupling)
     d64, e64 = _acc.exact_input(d, e, prec)
-    W0, Z0, st0 = _solve(d, e, prec, mode)
+    kw = {"gaptol": gaptol} if gaptol > 0 else {}
+    W0, Z0, st0 = _solve(d, e, prec, mode, **kw)
     assert st0["d_max"] >= 2 and st0["reps_backtracked"] == 0, st0["d_max"]
-    W, Z, st = _solve(d, e, prec, mode, flags=m.MRRR_FLAG_TEST_REJECT_CHILD)
+    W, Z, st = _solve(d, e, prec, mode, flags=m.MRRR_FLAG_TEST_REJECT_CHILD, **kw)
     assert st["reps_backtracked"] > 0 and st["reps_failed"] == 0, (st["reps_backtracked"], st["reps_failed"])
     assert np.all(np.diff(W) >= 0)
     _acc.check_eigvals(d64, e64, W, prec, mode)
