@@ -51,7 +51,7 @@ RQI_FLOPS = {"f64": (8.0, 3.0), "dd": (102.0, 22.0)}
 # DRAM bytes (read + write) per k_rqi launch on this workload, the mean over the
 # launches of one `ncu --set full` capture; valid only while the sources that
 # define the kernel hash to the value they had at the capture
-RQI_TRAFFIC = {"bytes_per_launch": 957.5e6, "sources_sha1": "f3d9c7e46fcc1075247d9a306e54fe13a65897d2",
+RQI_TRAFFIC = {"bytes_per_launch": 966.19e6, "sources_sha1": "773ead122fa8ed470d55f1f59a24cde7173a36d3",
                "sources": ("mrrr_core.cuh", "mrrr_dd.cuh", "mrrr_fast.cuh", "mrrr_phases.cuh", "mrrr_solver.cuh",
                            "mrrr_types.cuh", "solver_s.cu")}
 
@@ -417,7 +417,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     import paper_1304_1864_gb300 as m
     m.lib()
-    peak_meas, peak_ms = _probe_peak(m)
+    peak_meas, peak_ms = (None, None) if args.step_only else _probe_peak(m)
     mats_h = _workload()
     mats = [(torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev)) for d, e in mats_h]
     pairs_per_step = sum(d.shape[0] for d, _ in mats_h)
