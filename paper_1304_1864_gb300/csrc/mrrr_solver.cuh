@@ -134,6 +134,161 @@ __global__ void k_prep(MatrixDesc* mats, BlockDesc* blocks, double* wd, double* 
 
 // One CTA per block: the two candidate factorizations run on two warps, the
 // perturbation and derived data on all threads.
+// The leading principal minors of T - mu I for one root candidate, by one
+// thread: P_i = (a_i - mu) P_{i-1} - b_{i-1}^2 P_{i-2} with P_{-1} = 1,
+// P_{-2} = 0.  On entry D[i] = a_i - mu and L[i] = b_i^2; on exit D[i] = P_i,
+// and the pair (P_{i-1}, P_{i-2}) carried to the next row is rescaled by a
+// power of two (on the exponent fields) after every sixteenth row, whose
+// rescaled P_i goes to L[i] -- so row i + 1 divides by L[i] after such a row
+// and by D[i] after any other.  Two FP64 instructions per row on the chain.
+constexpr int kMinorGroup = 16;
+__device__ __forceinline__ void minor_chain(double* __restrict__ D, double* __restrict__ L, int n) {
+    double pm1 = 1.0, pm2 = 0.0, e2 = 0.0;
+    for (int i0 = 0; i0 < n; i0 += kMinorGroup) {
+        double t[kMinorGroup], e[kMinorGroup];
+#pragma unroll
+        for (int k = 0; k < kMinorGroup; ++k) {
+            const int i = min(i0 + k, n - 1);
+            t[k] = D[i];
+            e[k] = i < n - 1 ? L[i] : 0.0;
+        }
+        const int m = min(kMinorGroup, n - i0);
+#pragma unroll
+        for (int k = 0; k < kMinorGroup; ++k) {
+            if (k < m) {
+                const double P = fma(t[k], pm1, -(e2 * pm2));
+                D[i0 + k] = P;
+                pm2 = pm1;
+                pm1 = P;
+                e2 = e[k];
+            }
+        }
+        const int q = dnotnormal(pm1) ? 0 : dscale_exp(pm1);
+        pm1 = dscale_bits(pm1, q);
+        pm2 = dscale_bits(pm2, q);
+        if (m == kMinorGroup && i0 + m < n) L[i0 + m - 1] = pm1;
+    }
+}
+
+// Both root candidates of k_root (Algorithm 1, line 2: L D L^T = T - mu I
+// with mu just outside either end of the Gershgorin interval), in binary64,
+// by the whole block.  One thread per side runs the minors' recurrence
+// (minor_chain) on a_i - mu and b_i^2 formed beforehand by the block; then
+// every thread forms d_i = P_i / P_{i-1} and l_i = b_i / d_i, the growth
+// max |d_i| and the definiteness check (every pivot of the side's sign, none
+// zero or non-finite).  A side that fails retries further out (delta x 16),
+// as root_candidate does.  Rounding: d_i = P_i / P_{i-1} satisfies
+// d_i = (a_i - mu) - b_{i-1}^2 / d_{i-1} with both terms perturbed by a few
+// ulps, the mixed relative stability of the direct factorization; the random
+// perturbation xi = 4 eps_x that follows (root_element) is larger.  Against
+// one serial chain with a Newton reciprocal per row (about eight FP64
+// instructions), the chain is two.  For double-double reps the binary64
+// factors are then widened exactly, as in root_candidate.
+template <class Y>
+__device__ void root_candidates_block(const BlockDesc& B, const double* __restrict__ wd,
+                                      const double* __restrict__ we, Y* reps, double gl, double gu, double* s_g,
+                                      double* s_mu) {
+    constexpr int T = kRootThreads;
+    __shared__ double s_delta[2];
+    __shared__ int s_need[2], s_bad[2];
+    __shared__ unsigned long long s_gmax[2];
+    const int n = B.n;
+    const double* a = wd + B.row0;
+    const double* b = we + B.row0;
+    auto out = [&](int side) { return (double*)(reps + 4 * (size_t)B.row0 + (side ? 2 * (size_t)n : 0)); };
+    auto mu_of = [&](int side) { return side ? gu + s_delta[side] : gl - s_delta[side]; };
+    if (threadIdx.x < 2) {
+        s_delta[threadIdx.x] = 4.0 * n * 1.1102230246251565e-16 * fmax(fabs(gl), fabs(gu)) + 4.0 * B.pivmin;
+        s_need[threadIdx.x] = 1;
+    }
+    __syncthreads();
+    for (int attempt = 0; attempt < 40; ++attempt) {
+        const int need[2] = {s_need[0], s_need[1]};
+        if (!need[0] && !need[1]) break;
+        for (int side = 0; side < 2; ++side) {
+            if (!need[side]) continue;
+            const double mu = mu_of(side);
+            double* D = out(side);
+            for (int i = threadIdx.x; i < n; i += T) {
+                D[i] = a[i] - mu;
+                if (i < n - 1) D[n + i] = b[i] * b[i];
+            }
+        }
+        if (threadIdx.x < 2) {
+            s_bad[threadIdx.x] = 0;
+            s_gmax[threadIdx.x] = 0ULL;
+        }
+        __syncthreads();
+        if ((threadIdx.x == 0 && need[0]) || (threadIdx.x == 32 && need[1])) {
+            double* D = out(threadIdx.x == 32);
+            minor_chain(D, D + n, n);
+        }
+        __syncthreads();
+        for (int side = 0; side < 2; ++side) {
+            if (!need[side]) continue;
+            double* D = out(side);
+            double* L = D + n;
+            const int want = side ? 1 : 0;  // sign bit of every pivot
+            unsigned long long gmax = 0ULL;
+            int bad = 0;
+            // descending chunks: a chunk reads its own rows and the row below
+            // it before any of them is overwritten
+            for (int c0 = ((n - 1) / T) * T; c0 >= 0; c0 -= T) {
+                const int i = c0 + threadIdx.x;
+                double num = 0.0, den = 1.0;
+                if (i < n) {
+                    num = D[i];
+                    if (i > 0) den = ((i - 1) % kMinorGroup == kMinorGroup - 1) ? L[i - 1] : D[i - 1];
+                }
+                __syncthreads();
+                if (i < n) {
+                    const double d = num / den;
+                    const unsigned long long ab = dabsbits(d);
+                    bad |= (dsign(d) != want) | (ab == 0ULL) | !dfinite(d);
+                    gmax = ab > gmax ? ab : gmax;
+                    D[i] = d;
+                    L[i] = i < n - 1 ? b[i] / d : 0.0;
+                }
+                __syncthreads();
+            }
+            if (bad) atomicOr(&s_bad[side], 1);
+            atomicMax(&s_gmax[side], gmax);
+        }
+        __syncthreads();
+        if (threadIdx.x < 2 && need[threadIdx.x]) {
+            const int side = threadIdx.x;
+            if (!s_bad[side]) {
+                s_g[side] = __longlong_as_double((long long)s_gmax[side]);
+                s_mu[side] = mu_of(side);
+                s_need[side] = 0;
+            } else {
+                s_delta[side] *= 16.0;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2 && s_need[threadIdx.x]) {
+        s_g[threadIdx.x] = INFINITY;
+        s_mu[threadIdx.x] = mu_of(threadIdx.x);
+    }
+    if constexpr (std::is_same<Y, dd>::value) {
+        // widen both sides in place: double-double entry i covers binary64
+        // words 2i, 2i+1 >= i, so descending chunks read before they write
+        for (int side = 0; side < 2; ++side) {
+            Y* rep = reps + 4 * (size_t)B.row0 + (side ? 2 * (size_t)n : 0);
+            const double* src = (const double*)rep;
+            for (int c0 = ((2 * n - 1) / T) * T; c0 >= 0; c0 -= T) {
+                const int i = c0 + threadIdx.x;
+                const double v = i < 2 * n ? src[i] : 0.0;
+                __syncthreads();
+                if (i < 2 * n) rep[i] = dd(v);
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <class Y, class Lo>
 __global__ void k_root(const int* blist, BlockDesc* blocks, const MatrixDesc* mats, const double* wd,
                        const double* we, Y* reps, Lo* reps_lo, SolveCfg cfg) {
@@ -173,9 +328,13 @@ __global__ void k_root(const int* blist, BlockDesc* blocks, const MatrixDesc* ma
         }
         return;
     }
-    if (threadIdx.x == 0 || threadIdx.x == 32) {
-        int side = threadIdx.x == 32;
-        s_g[side] = root_candidate<Y>(B, wd, we, reps, s_gl, s_gu, side, &s_mu[side]);
+    if constexpr (std::is_same<Y, double>::value || std::is_same<Y, dd>::value) {
+        root_candidates_block<Y>(B, wd, we, reps, s_gl, s_gu, s_g, s_mu);
+    } else {
+        if (threadIdx.x == 0 || threadIdx.x == 32) {
+            int side = threadIdx.x == 32;
+            s_g[side] = root_candidate<Y>(B, wd, we, reps, s_gl, s_gu, side, &s_mu[side]);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) root_choose(B, M, s_gl, s_gu, s_g[0], s_mu[0], s_g[1], s_mu[1], cfg);
