@@ -566,12 +566,13 @@ __global__ void k_verify(Item* items, const int* list, int count, const BlockDes
 
 // kFixLanes lanes per listed item move its failing ends.  For a failing
 // lower end x (count(x) >= j) the lanes test, in one sweep, the points
-// x - w 4^k for k = 1..kFixLanes; the point nearest to x whose count is < j
+// x - w 4^k for k = 0..kFixLanes-1; the point nearest to x whose count is < j
 // is the new lower end, and the point tested just before it -- whose count
 // is still >= j, so it bounds lambda_j from above -- the new upper end when
 // that end did not fail too.  Symmetrically for a failing upper end.  w is
 // the first doubling step of the sequential check (endpoint_step), so the
-// sweep covers sixteen doublings with the latency of one count.  Beyond
+// sweep covers fourteen doublings with the latency of one count (the first
+// point, one bracket width out, is where most ends that failed end up).  Beyond
 // that the end falls back to the sequential widening, which ends at the
 // bound of the whole spectrum.
 constexpr int kFixLanes = 8;
@@ -601,7 +602,7 @@ __global__ void k_verify_fix(Item* items, const int* fix_list, int bound, const 
         bool found = false;
         double p = x0;
         for (int sw = 0; sw < kFixSweeps && !found; ++sw) {
-            double f = ldexp(1.0, 2 * (sw * kFixLanes + q + 1));  // 4^(k)
+            double f = ldexp(1.0, 2 * (sw * kFixLanes + q));  // 4^(k-1)
             double xq = side ? x0 + w0[side] * f : x0 - w0[side] * f;
             int c = count_at<Y, true>(rep, rep + 3 * n, n, from_d<Y>(xq), pm);
             steps += (unsigned long long)n;
@@ -992,7 +993,12 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
     typedef typename LowOf<Y>::T Lo;
     const bool use_low = LowOf<Y>::use && !(cfg.flags & MRRR_FLAG_NO_LOWPREC_BISECT);
     // relative width of the low-precision pre-bisection
+    // relative width at which the low-precision pre-bisection stops: about
+    // 8 units of binary32 at the root level (the brackets that pass the
+    // working-precision check go to the RQI as they are, and a narrower one
+    // needs fewer RQI steps), about 32 units below it
     const double wrel_lo = std::is_same<Lo, float>::value ? 0x1p-19 : cfg.rtol_class;
+    const double wrel_root = std::is_same<Lo, float>::value ? 0x1p-21 : cfg.rtol_class;
     long long N = 0;
     int nmax = 1;
     for (int p = 0; p < P; ++p) {
@@ -1082,7 +1088,7 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 int launches = 0;
                 if (use_low) {
                     k_bisect_lo_ms<Lo><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(
-                        items, list, count, d_blocks, wrel_lo, d_C);
+                        items, list, count, d_blocks, phase == MRRR_PHASE_BISECT ? wrel_root : wrel_lo, d_C);
                     MRRR_CK(cudaMemsetAsync(&d_C->nvfix, 0, sizeof(int), st));
                     k_verify<Y><<<grid_for(2LL * count, kLatThreads), kLatThreads, 0, st>>>(
                         items, list, count, d_blocks, d_C, ctr, vflags, vfix_list);
