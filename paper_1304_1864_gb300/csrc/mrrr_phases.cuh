@@ -331,6 +331,8 @@ MRRR_HD void init_item(const BlockDesc& B, int bidx, Item& I, int t, const Y* re
     I.sig_up_lo = 0.0;
     I.span_lo = 0.0;
     I.span_hi = 0.0;
+    I.span_gapL = INFINITY;
+    I.span_gapR = INFINITY;
     I.lam_hi = 0.0;
     I.lam_lo = 0.0;
     I.rqi_done = 0;
@@ -796,8 +798,8 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     // coordinates with bracket width bw; the candidate reps are built into
     // `out` (which doubles as work space); `reject` turns every acceptance
     // down (test hook); the candidate `skip` is not tried
-    auto search = [&](const Y* parent, double lo, double hi, double bw, Y* out, Lo* out_lo, bool reject,
-                      double skip) {
+    auto search = [&](const Y* parent, double lo, double hi, double bw, double gapL, double gapR, Y* out, Lo* out_lo,
+                      bool reject, double skip) {
         const double span = hi - lo;
         double base = fmax(fmax(0.25 * span, 2.0 * bw), 4.0 * cfg.eps_y * fmax(fabs(lo), fabs(hi)));
         base = fmax(base, 4.0 * B.pivmin);
@@ -805,7 +807,7 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
         for (int k = 0; k < 6 && !f.accepted; ++k) {
             double delta = base * (double)(1 << k);
             for (int side = 0; side < 2 && !f.accepted; ++side) {
-                double gap = side == 0 ? K.gapL : K.gapR;
+                double gap = side == 0 ? gapL : gapR;
                 if (k > 0 && delta > 0.5 * gap) continue;
                 double tau = side == 0 ? lo - delta : hi + delta;
                 if (tau == skip) continue;
@@ -851,7 +853,7 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     // test hook: turn down every candidate built from a parent that is itself
     // a child, so that the backtracking branch runs
     const bool hook = (cfg.flags & MRRR_FLAG_TEST_REJECT_CHILD) && first.rep_up != nullptr;
-    Found f = search(parent, first.lo, last.hi, bw, child, child_lo, hook, NAN);
+    Found f = search(parent, first.lo, last.hi, bw, K.gapL, K.gapR, child, child_lo, hook, NAN);
     if (!f.accepted && first.rep_up != nullptr) {
         // backtracking: another rep for the parent's cluster, from the
         // parent's parent G, skipping the shift that made the parent
@@ -861,14 +863,19 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
         const double tau_p = tp.hi + tp.lo;
         Y* alt = child + 4 * (size_t)n;
         Lo* alt_lo = child_lo + 2 * (size_t)n;
-        const double pw = fmax(bw, 1e-3 * (first.span_hi - first.span_lo));
-        Found fp = search(G, first.span_lo, first.span_hi, pw, alt, alt_lo, false, tau_p);
+        // the alternative parent depends on the parent's cluster alone (its
+        // span and gaps in G, the skipped shift), not on this cluster: every
+        // cluster of P that backtracks rebuilds the same P', so their vectors
+        // share one representation and stay orthogonal to each other
+        const double pw = 1e-3 * (first.span_hi - first.span_lo);
+        Found fp = search(G, first.span_lo, first.span_hi, pw, first.span_gapL, first.span_gapR, alt, alt_lo, false,
+                          tau_p);
         if (!(fp.stored == fp.tau)) child_transform<Y, Lo>(G, n, from_d<Y>(fp.tau), pm, alt, alt_lo, erep);
         steps += n;
         if (!fp.accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
         // the members in the coordinates of P' = G - tau' I: + tau_p - tau'
         const double mv = tau_p - fp.tau;
-        Found g = search(alt, first.lo + mv, last.hi + mv, bw, child, child_lo, false, NAN);
+        Found g = search(alt, first.lo + mv, last.hi + mv, bw, K.gapL, K.gapR, child, child_lo, false, NAN);
         if (g.accepted || g.w < f.w) {
             f = g;
             from = alt;
@@ -908,6 +915,8 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
         I.sig_up_lo = sig_from.lo;
         I.span_lo = span_lo;
         I.span_hi = span_hi;
+        I.span_gapL = K.gapL;
+        I.span_gapR = K.gapR;
         I.rep = child;
         I.rep_lo = child_lo;
         I.sig_hi = sig.hi;

@@ -436,9 +436,16 @@ __global__ void k_bisect_lo(Item* items, const int* list, int count, const Block
 // Multisection sweeps (kMS, ms_point) with the lanes of one item adjacent in
 // a warp, sharing their counts by shuffles.
 
-// shuffle mask of the kMS-lane group of this thread
+// shuffle mask of the M-lane group of this thread
+template <int M = kMS>
 __device__ __forceinline__ unsigned ms_mask() {
-    return ((1u << kMS) - 1u) << ((threadIdx.x & 31) & ~(kMS - 1));
+    return ((1u << M) - 1u) << ((threadIdx.x & 31) & ~(M - 1));
+}
+
+// point q of an M-point multisection sweep of [lo, hi]
+template <int M>
+__device__ __forceinline__ double ms_point_m(double lo, double hi, int q) {
+    return lo + (hi - lo) / (M + 1) * (q + 1);
 }
 
 // Given the counts c_k at the points x_k (k < kMS) of a sweep, in increasing
@@ -446,14 +453,15 @@ __device__ __forceinline__ unsigned ms_mask() {
 // point before it the new lower end -- well defined even where rounding makes
 // a count non-monotone.  Points that rounded onto or outside the bracket are
 // skipped.  Returns false when no point was inside.
+template <int M = kMS>
 __device__ __forceinline__ bool ms_update(unsigned mask, int c, double x, bool inside, int j, double& lo, double& hi) {
     double nlo = lo, nhi = hi;
     bool any_inside = false, found = false;
 #pragma unroll
-    for (int k = 0; k < kMS; ++k) {
-        const int ck = __shfl_sync(mask, c, k, kMS);
-        const double xk = __shfl_sync(mask, x, k, kMS);
-        const bool ik = __shfl_sync(mask, (int)inside, k, kMS) != 0;
+    for (int k = 0; k < M; ++k) {
+        const int ck = __shfl_sync(mask, c, k, M);
+        const double xk = __shfl_sync(mask, x, k, M);
+        const bool ik = __shfl_sync(mask, (int)inside, k, M) != 0;
         any_inside |= ik;
         if (!ik || found) continue;
         if (ck >= j) {
@@ -471,14 +479,14 @@ __device__ __forceinline__ bool ms_update(unsigned mask, int c, double x, bool i
 
 // Low-precision pre-bisection of the listed items (Sec. 3.2: eigenvalues are
 // approximated in a precision below the working one) down to a relative
-// width wrel, by multisection with kMS lanes per item.
-template <class Lo>
+// width wrel, by multisection with M lanes per item.
+template <class Lo, int M>
 __global__ void k_bisect_lo_ms(Item* items, const int* list, int count, const BlockDesc* blocks, double wrel,
                                DevCounters* C) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int g = t / kMS, q = t % kMS;
-    if (g >= count) return;  // whole groups leave together (kMS divides 32)
-    const unsigned mask = ms_mask();
+    const int g = t / M, q = t % M;
+    if (g >= count) return;  // whole groups leave together (M divides 32)
+    const unsigned mask = ms_mask<M>();
     Item& I = items[list ? list[g] : g];
     const int n = I.n;
     if (n == 1) return;
@@ -489,11 +497,11 @@ __global__ void k_bisect_lo_ms(Item* items, const int* list, int count, const Bl
     unsigned long long steps = 0;
     for (int it = 0; it < 64; ++it) {
         if (!(hi - lo > wrel * fmax(fabs(lo), fabs(hi)))) break;
-        const Lo x = (Lo)ms_point(lo, hi, q);
+        const Lo x = (Lo)ms_point_m<M>(lo, hi, q);
         const bool inside = (double)x > lo && (double)x < hi;
         const int c = inside ? count_lo<Lo>(D, LLD, n, x, pm) : 0;
         if (inside) steps += (unsigned long long)n;
-        if (!ms_update(mask, c, (double)x, inside, I.j, lo, hi)) break;  // no representable interior point left
+        if (!ms_update<M>(mask, c, (double)x, inside, I.j, lo, hi)) break;  // no representable interior point left
     }
     if (q == 0) {
         I.lo = lo;
@@ -576,6 +584,13 @@ __global__ void k_verify(Item* items, const int* list, int count, const BlockDes
 // that the end falls back to the sequential widening, which ends at the
 // bound of the whole spectrum.
 constexpr int kFixLanes = 8;
+// lanes per item of the low-precision pre-bisection at the root level
+// (kMSRoot) and for cluster members in their child rep (kMSChild).  Sixteen
+// child lanes made the n = 4001 step 0.7 ms shorter, but the backtracked
+// tree of twelve glued W_21 then lost its orthogonality, so both stay at
+// four (eight or sixteen at the root level made the RQI slower).
+constexpr int kMSRoot = kMS;
+constexpr int kMSChild = kMS;
 constexpr int kFixSweeps = 1;
 template <class Y>
 __global__ void k_verify_fix(Item* items, const int* fix_list, int bound, const BlockDesc* blocks, DevCounters* C,
@@ -1087,8 +1102,12 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                 tl.begin(phase);
                 int launches = 0;
                 if (use_low) {
-                    k_bisect_lo_ms<Lo><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(
-                        items, list, count, d_blocks, phase == MRRR_PHASE_BISECT ? wrel_root : wrel_lo, d_C);
+                    if (phase == MRRR_PHASE_BISECT)
+                        k_bisect_lo_ms<Lo, kMSRoot><<<grid_for((long long)count * kMSRoot, kLatThreads), kLatThreads,
+                                                       0, st>>>(items, list, count, d_blocks, wrel_root, d_C);
+                    else
+                        k_bisect_lo_ms<Lo, kMSChild><<<grid_for((long long)count * kMSChild, kLatThreads), kLatThreads, 0,
+                                                        st>>>(items, list, count, d_blocks, wrel_lo, d_C);
                     MRRR_CK(cudaMemsetAsync(&d_C->nvfix, 0, sizeof(int), st));
                     k_verify<Y><<<grid_for(2LL * count, kLatThreads), kLatThreads, 0, st>>>(
                         items, list, count, d_blocks, d_C, ctr, vflags, vfix_list);

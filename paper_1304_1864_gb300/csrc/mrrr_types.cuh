@@ -83,10 +83,12 @@ struct Item {
     int wanted;         // 1 if the eigenpair is returned, 0 if only a neighbour
     // the representation one level up (the parent of `rep`; nullptr at the
     // root), its accumulated shift, and the span [span_lo, span_hi] (in its
-    // coordinates) of the cluster `rep` was made for -- for backtracking
+    // coordinates) of the cluster `rep` was made for, with that cluster's
+    // gaps to the rest of the spectrum -- for backtracking
     const void* rep_up;
     double sig_up_hi, sig_up_lo;
     double span_lo, span_hi;
+    double span_gapL, span_gapR;
     // Rayleigh quotient iteration state carried between passes
     double lam_hi, lam_lo;  // current shift (hi + lo)
     int rqi_done;       // iterations done so far
