@@ -584,13 +584,15 @@ __global__ void k_verify(Item* items, const int* list, int count, const BlockDes
 // that the end falls back to the sequential widening, which ends at the
 // bound of the whole spectrum.
 constexpr int kFixLanes = 8;
-// lanes per item of the low-precision pre-bisection at the root level
-// (kMSRoot) and for cluster members in their child rep (kMSChild).  Sixteen
-// child lanes made the n = 4001 step 0.7 ms shorter, but the backtracked
-// tree of twelve glued W_21 then lost its orthogonality, so both stay at
-// four (eight or sixteen at the root level made the RQI slower).
+// lanes per item of the low-precision pre-bisection: kMSRoot at the root
+// level; kMSChild for cluster members in their child rep, which start from
+// brackets many orders of magnitude wider than their eigenvalues (the
+// parent's brackets, shifted) -- sixteen points per sweep take fewer sweeps,
+// and leave brackets from which fewer eigenpairs need a third RQI step
+// (measured on the n = 4001 step: 15.0 ms against 15.7 ms with four; eight
+// or sixteen at the root level made the RQI slower)
 constexpr int kMSRoot = kMS;
-constexpr int kMSChild = kMS;
+constexpr int kMSChild = 16;
 constexpr int kFixSweeps = 1;
 template <class Y>
 __global__ void k_verify_fix(Item* items, const int* fix_list, int bound, const BlockDesc* blocks, DevCounters* C,

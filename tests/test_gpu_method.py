@@ -194,22 +194,26 @@ def test_variant_paths_n4001(flag):
             assert st["reps_failed"] == 0
 
 
-@pytest.mark.parametrize("prec,mode,coupling,gaptol", [("d", "plain", 1e-8, 0.0), ("s", "mixed", 1e-5, 1e-3)])
-def test_backtracking_forced_by_the_test_hook(prec, mode, coupling, gaptol):
-    # twelve W_21 blocks glued together have clusters inside clusters: the
-    # top eigenvalues of the copies form three groups, each of nearly equal
-    # eigenvalues (gaps of a few units of 1e-15), about 0.6 x coupling apart.
-    # With gaptol 1e-3 (the plain binary64 default; set through the
-    # parameter block for the binary32/binary64 solver, whose default 1e-5
-    # resolves these groups in one level) the groups fall into one cluster at
-    # the root and each group is a cluster again in the child made for the
-    # whole set (d_max >= 2).  The test hook turns down every child
-    # representation built from a child, so each such cluster must be
+@pytest.mark.parametrize("prec,mode,coupling,delta,gaptol",
+                         [("d", "plain", 1e-8, 1e-6, 0.0), ("s", "mixed", 1.5e-6, 1e-4, 1e-3)])
+def test_backtracking_forced_by_the_test_hook(prec, mode, coupling, delta, gaptol):
+    # twelve W_21 blocks glued together, block c shifted by c * delta: the
+    # top pairs of the twelve copies (each pair a few 1e-11 apart for binary64
+    # input, a few 1e-8 for binary32) form one cluster at the root, and each
+    # pair is a cluster again in the child made for the whole set (d_max >= 2).
+    # The shifts keep the pairs apart; without them the symmetric gluing makes
+    # a pair whose gap is below binary64 resolution (zero even in binary128),
+    # whose two vectors no tree of binary64 representations can make
+    # orthogonal.  gaptol is 1e-3 (the plain binary64 default; set through
+    # the parameter block for the binary32/binary64 solver, whose default
+    # 1e-5 resolves the groups in one level).  The test hook turns down every
+    # child representation built from a child, so each pair's cluster must be
     # processed again with another shift one level up (backtracking, Sec.
     # 3.2, "The representation tree"); the results still meet the targets of
     # the mode and every eigenvalue matches the oracle.
     import paper_1304_1864_gb300 as m
     d, e = inputs.glued_wilkinson(12, 21, coupling)
+    d = d + np.repeat(np.arange(12) * delta, 21)
     d64, e64 = _acc.exact_input(d, e, prec)
     kw = {"gaptol": gaptol} if gaptol > 0 else {}
     W0, Z0, st0 = _solve(d, e, prec, mode, **kw)
@@ -219,7 +223,7 @@ def test_backtracking_forced_by_the_test_hook(prec, mode, coupling, gaptol):
     assert np.all(np.diff(W) >= 0)
     _acc.check_eigvals(d64, e64, W, prec, mode)
     r1, o1 = _acc.check_res_orth(d64, e64, W, Z, prec, mode)
-    r0, o0 = _acc.measure_res_orth(d64, e64, W0, Z0, prec)
+    r0, o0 = _acc.check_res_orth(d64, e64, W0, Z0, prec, mode)
     print("%s %s res/orth (n eps): tree %.3g / %.3g, backtracked %.3g / %.3g" % (prec, mode, r0, o0, r1, o1))
 
 
