@@ -590,9 +590,14 @@ constexpr int kFixLanes = 8;
 // parent's brackets, shifted) -- sixteen points per sweep take fewer sweeps,
 // and leave brackets from which fewer eigenpairs need a third RQI step
 // (measured on the n = 4001 step: 15.0 ms against 15.7 ms with four; eight
-// or sixteen at the root level made the RQI slower)
+// or sixteen at the root level made the RQI slower).  Only while the list is
+// short enough to leave SM sub-partitions idle, and only for a binary32
+// count: a batch of thousands of matrices (6.0M against 6.4M eigenpairs/s)
+// and the binary64 pre-bisection of the double-double solver were slower
+// with sixteen.
 constexpr int kMSRoot = kMS;
 constexpr int kMSChild = 16;
+constexpr int kMSChildMaxItems = 32768;
 constexpr int kFixSweeps = 1;
 template <class Y>
 __global__ void k_verify_fix(Item* items, const int* fix_list, int bound, const BlockDesc* blocks, DevCounters* C,
@@ -1107,9 +1112,12 @@ int solve_batch(int P, MatrixDesc* mats, const SolveCfg& cfg, int max_depth, cud
                     if (phase == MRRR_PHASE_BISECT)
                         k_bisect_lo_ms<Lo, kMSRoot><<<grid_for((long long)count * kMSRoot, kLatThreads), kLatThreads,
                                                        0, st>>>(items, list, count, d_blocks, wrel_root, d_C);
-                    else
+                    else if (std::is_same<Lo, float>::value && count <= kMSChildMaxItems)
                         k_bisect_lo_ms<Lo, kMSChild><<<grid_for((long long)count * kMSChild, kLatThreads), kLatThreads, 0,
                                                         st>>>(items, list, count, d_blocks, wrel_lo, d_C);
+                    else
+                        k_bisect_lo_ms<Lo, kMS><<<grid_for((long long)count * kMS, kLatThreads), kLatThreads, 0, st>>>(
+                            items, list, count, d_blocks, wrel_lo, d_C);
                     MRRR_CK(cudaMemsetAsync(&d_C->nvfix, 0, sizeof(int), st));
                     k_verify<Y><<<grid_for(2LL * count, kLatThreads), kLatThreads, 0, st>>>(
                         items, list, count, d_blocks, d_C, ctr, vflags, vfix_list);
