@@ -59,7 +59,8 @@ typedef enum {
     MRRR_ERR_NOMEM = -4,      /* device allocation failed */
     MRRR_ERR_CUDA = -5,       /* CUDA runtime error / no device */
     MRRR_ERR_TIMEOUT = -6,    /* a bounded device-side wait ran out */
-    MRRR_ERR_NOREP = -7       /* informational: no candidate passed the representation test */
+    MRRR_ERR_NOREP = -7,      /* informational: no candidate passed the representation test */
+    MRRR_ERR_CANCELLED = -8   /* serving: the request was cancelled before it ran */
 } mrrr_status;
 
 /* Phases of a solve, indexing mrrr_stats.phase_ms. */
@@ -133,6 +134,10 @@ typedef struct {
                                          of the cluster's eigenvalues along an approximate cluster vector is
                                          within the k_rr bound: 10, or with y > x the relaxed bound
                                          max{10, eps_x gaptol / (eps_y sqrt(n))} of Sec. 3.2, Eq. (3.7) */
+#define MRRR_FLAG_TEST_NO_REP 256     /* testing only: turn down every candidate representation, in the
+                                         first search and in backtracking, so that every cluster takes its
+                                         best failed candidate (the branch of Algorithm 1, lines 15-17, for
+                                         "no suitable representation"; counted in reps_failed) */
 #define MRRR_FLAG_TEST_REJECT_CHILD 32 /* testing only: turn down every child representation built from a
                                           parent that is itself a child, which forces the backtracking
                                           branch of the representation tree (Sec. 3.2) */
@@ -300,6 +305,9 @@ typedef struct {
     int workers;          /* concurrent batches (host threads + streams) [2] */
     int max_batch;        /* requests per batch [512] */
     long long hbm_budget; /* device bytes for admitted requests; 0: half the free memory at open */
+    int alloc_failures;   /* testing only: the first alloc_failures batches fail as if their device
+                             allocation had failed (every request in them completes with
+                             MRRR_ERR_NOMEM; the server goes on) [0] */
 } mrrr_serve_config;
 
 typedef struct {
@@ -344,7 +352,13 @@ int mrrr_serve_submit(mrrr_server* s, const mrrr_request* req, long long* ticket
    if it is not complete, else its status, fills *info (may be NULL) and
    retires the ticket.  An unknown ticket returns MRRR_ERR_ARG. */
 int mrrr_serve_poll(mrrr_server* s, long long ticket, int wait_ms, mrrr_serve_info* info);
-/* Latency and throughput counters since open. */
+/* Withdraw a request that has not been admitted yet: returns MRRR_OK, and its
+   poll then returns MRRR_ERR_CANCELLED with the output buffers untouched.  A
+   request already admitted or completed is not withdrawn: MRRR_PENDING (poll
+   it for its result).  An unknown or retired ticket returns MRRR_ERR_ARG. */
+int mrrr_serve_cancel(mrrr_server* s, long long ticket);
+/* Latency and throughput counters since open (cancelled requests are not
+   counted). */
 int mrrr_serve_stats_get(mrrr_server* s, mrrr_serve_stats* out);
 /* Finish every queued request, stop the workers and free the server. */
 int mrrr_serve_close(mrrr_server* s);

@@ -16,8 +16,10 @@ MRRR_ALL, MRRR_INDEX, MRRR_VALUE = 0, 1, 2
 MRRR_PLAIN, MRRR_MIXED = 0, 1
 MRRR_OK, MRRR_ERR_ARG, MRRR_ERR_NONFINITE, MRRR_ERR_NOCONV = 0, -1, -2, -3
 MRRR_ERR_NOMEM, MRRR_ERR_CUDA, MRRR_ERR_TIMEOUT, MRRR_ERR_NOREP = -4, -5, -6, -7
+MRRR_ERR_CANCELLED = -8
 MRRR_FLAG_NO_LOWPREC_BISECT, MRRR_FLAG_TIMING, MRRR_FLAG_STRICT_GROWTH, MRRR_FLAG_NO_TUNE = 1, 4, 8, 16
 MRRR_FLAG_TEST_REJECT_CHILD, MRRR_FLAG_E_REP, MRRR_FLAG_RRR_TEST = 32, 64, 128
+MRRR_FLAG_TEST_NO_REP = 256
 NPHASES = 8
 PHASES = ("prep", "root", "bisect", "classify", "shift", "refine", "rqi", "finish")
 
@@ -50,7 +52,8 @@ MRRR_PENDING = 1
 
 
 class MrrrServeConfig(ctypes.Structure):
-    _fields_ = [("workers", ctypes.c_int), ("max_batch", ctypes.c_int), ("hbm_budget", ctypes.c_longlong)]
+    _fields_ = [("workers", ctypes.c_int), ("max_batch", ctypes.c_int), ("hbm_budget", ctypes.c_longlong),
+                ("alloc_failures", ctypes.c_int)]
 
 
 class MrrrRequest(ctypes.Structure):
@@ -117,6 +120,7 @@ def lib():
         L.mrrr_serve_submit.argtypes = [vp, ctypes.POINTER(MrrrRequest), ctypes.POINTER(ctypes.c_longlong)]
         L.mrrr_serve_poll.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(MrrrServeInfo)]
         L.mrrr_serve_stats_get.argtypes = [vp, ctypes.POINTER(MrrrServeStats)]
+        L.mrrr_serve_cancel.argtypes = [vp, ctypes.c_longlong]
         L.mrrr_serve_close.argtypes = [vp]
         for name in ("mrrr_serve_open", "mrrr_serve_submit", "mrrr_serve_poll", "mrrr_serve_stats_get",
                      "mrrr_serve_close"):
@@ -187,6 +191,10 @@ def mrrr_serve_submit(server, req, ticket):
 
 def mrrr_serve_poll(server, ticket, wait_ms, info):
     return lib().mrrr_serve_poll(server, ticket, wait_ms, info)
+
+
+def mrrr_serve_cancel(server, ticket):
+    return lib().mrrr_serve_cancel(server, ticket)
 
 
 def mrrr_serve_stats_get(server, out):
@@ -400,9 +408,9 @@ class Server:
     referenced until the ticket is polled.  poll() returns (status, info dict)
     or None while the request is pending."""
 
-    def __init__(self, workers=0, max_batch=0, hbm_budget=0):
+    def __init__(self, workers=0, max_batch=0, hbm_budget=0, alloc_failures=0):
         self._h = ctypes.c_void_p()
-        cfg = MrrrServeConfig(workers, max_batch, hbm_budget)
+        cfg = MrrrServeConfig(workers, max_batch, hbm_budget, alloc_failures)
         rc = lib().mrrr_serve_open(ctypes.byref(cfg), ctypes.byref(self._h))
         if rc != MRRR_OK:
             raise MrrrError(rc, "mrrr_serve_open")
@@ -431,6 +439,14 @@ class Server:
             raise MrrrError(rc, "mrrr_serve_poll")
         self._keep.pop(ticket, None)
         return rc, {f: getattr(info, f) for f, _ in info._fields_}
+
+    def cancel(self, ticket):
+        """MRRR_OK if the request was withdrawn before it ran, MRRR_PENDING if
+        it was already admitted (poll it)."""
+        rc = lib().mrrr_serve_cancel(self._h, ticket)
+        if rc == MRRR_ERR_ARG:
+            raise MrrrError(rc, "mrrr_serve_cancel")
+        return rc
 
     def stats(self):
         st = MrrrServeStats()

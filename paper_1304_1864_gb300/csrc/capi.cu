@@ -597,6 +597,7 @@ const char* mrrr_strerror(int status) {
         case MRRR_ERR_CUDA: return "CUDA runtime error or no CUDA device";
         case MRRR_ERR_TIMEOUT: return "a bounded device-side wait ran out";
         case MRRR_ERR_NOREP: return "no candidate representation passed the acceptance test";
+        case MRRR_ERR_CANCELLED: return "the request was cancelled before it ran";
         default: return "unknown status";
     }
 }

@@ -853,7 +853,10 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
     // test hook: turn down every candidate built from a parent that is itself
     // a child, so that the backtracking branch runs
     const bool hook = (cfg.flags & MRRR_FLAG_TEST_REJECT_CHILD) && first.rep_up != nullptr;
-    Found f = search(parent, first.lo, last.hi, bw, K.gapL, K.gapR, child, child_lo, hook, NAN);
+    // test hook: turn down every candidate (the "no suitable representation"
+    // branch: the best failed candidate is taken)
+    const bool no_rep = (cfg.flags & MRRR_FLAG_TEST_NO_REP) != 0;
+    Found f = search(parent, first.lo, last.hi, bw, K.gapL, K.gapR, child, child_lo, hook || no_rep, NAN);
     if (!f.accepted && first.rep_up != nullptr) {
         // backtracking: another rep for the parent's cluster, from the
         // parent's parent G, skipping the shift that made the parent
@@ -868,14 +871,14 @@ MRRR_HD void shift_cluster(const Cluster& K, Item* items, const BlockDesc* block
         // cluster of P that backtracks rebuilds the same P', so their vectors
         // share one representation and stay orthogonal to each other
         const double pw = 1e-3 * (first.span_hi - first.span_lo);
-        Found fp = search(G, first.span_lo, first.span_hi, pw, first.span_gapL, first.span_gapR, alt, alt_lo, false,
+        Found fp = search(G, first.span_lo, first.span_hi, pw, first.span_gapL, first.span_gapR, alt, alt_lo, no_rep,
                           tau_p);
         if (!(fp.stored == fp.tau)) child_transform<Y, Lo>(G, n, from_d<Y>(fp.tau), pm, alt, alt_lo, erep);
         steps += n;
         if (!fp.accepted) MRRR_ATOMIC_ADD(&C->reps_failed, 1);
         // the members in the coordinates of P' = G - tau' I: + tau_p - tau'
         const double mv = tau_p - fp.tau;
-        Found g = search(alt, first.lo + mv, last.hi + mv, bw, K.gapL, K.gapR, child, child_lo, false, NAN);
+        Found g = search(alt, first.lo + mv, last.hi + mv, bw, K.gapL, K.gapR, child, child_lo, no_rep, NAN);
         if (g.accepted || g.w < f.w) {
             f = g;
             from = alt;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -86,6 +87,7 @@ struct mrrr_server {
     std::vector<std::thread> workers;
     std::vector<double> latencies;
     long long eigenpairs = 0, batches = 0;
+    std::atomic<int> alloc_failures{0};  // test hook: batches still to fail as out of memory
     bool started = false;
     Clock::time_point t_first, t_last;
 
@@ -118,6 +120,8 @@ void mrrr_server::run_batch(std::vector<Req*>& batch, cudaStream_t st, char*& pi
     int rc = MRRR_OK;
     char* din = nullptr;
     char* dout = nullptr;
+    // test hook: this batch fails as if its device allocation had
+    if (alloc_failures.load() > 0 && alloc_failures.fetch_sub(1) > 0) rc = MRRR_ERR_NOMEM;
     // device buffers: after the caller's work queued before submit
     for (int p = 0; p < nb && rc == MRRR_OK; ++p)
         if (batch[p]->ready && cudaStreamWaitEvent(st, batch[p]->ready, 0) != cudaSuccess) rc = MRRR_ERR_CUDA;
@@ -301,6 +305,7 @@ extern "C" int mrrr_serve_open(const mrrr_serve_config* cfg, mrrr_server** out) 
     s->cfg = c;
     s->device = dev;
     s->budget = (size_t)c.hbm_budget;
+    s->alloc_failures = std::max(c.alloc_failures, 0);
     for (int w = 0; w < c.workers; ++w) s->workers.emplace_back([s] { s->worker_main(); });
     *out = s;
     return MRRR_OK;
@@ -374,6 +379,25 @@ extern "C" int mrrr_serve_poll(mrrr_server* s, long long ticket, int wait_ms, mr
     s->live.erase(it);
     delete q;
     return st;
+}
+
+extern "C" int mrrr_serve_cancel(mrrr_server* s, long long ticket) {
+    if (!s) return MRRR_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->live.find(ticket);
+        if (it == s->live.end()) return MRRR_ERR_ARG;
+        Req* q = it->second;
+        auto p = std::find(s->pending.begin(), s->pending.end(), q);
+        if (p == s->pending.end()) return MRRR_PENDING;  // admitted or done: poll it
+        s->pending.erase(p);
+        q->status = MRRR_ERR_CANCELLED;
+        q->t_admit = q->t_done = Clock::now();
+        q->done = true;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+    return MRRR_OK;
 }
 
 extern "C" int mrrr_serve_stats_get(mrrr_server* s, mrrr_serve_stats* out) {

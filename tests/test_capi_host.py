@@ -144,9 +144,10 @@ def test_serve_arguments_rejected_without_device_work():
     assert L.mrrr_serve_submit(None, ctypes.byref(req), ctypes.byref(t)) == m.MRRR_ERR_ARG
     assert L.mrrr_serve_poll(None, 1, 0, None) == m.MRRR_ERR_ARG
     assert L.mrrr_serve_stats_get(None, None) == m.MRRR_ERR_ARG
+    assert L.mrrr_serve_cancel(None, 1) == m.MRRR_ERR_ARG
     assert L.mrrr_serve_close(None) == m.MRRR_ERR_ARG
     assert L.mrrr_serve_open(None, None) == m.MRRR_ERR_ARG
-    bad = m.MrrrServeConfig(-1, 0, 0)
+    bad = m.MrrrServeConfig(-1, 0, 0, 0)
     h = ctypes.c_void_p()
     assert L.mrrr_serve_open(ctypes.byref(bad), ctypes.byref(h)) == m.MRRR_ERR_ARG
 

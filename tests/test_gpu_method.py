@@ -227,6 +227,25 @@ def test_backtracking_forced_by_the_test_hook(prec, mode, coupling, delta, gapto
     print("%s %s res/orth (n eps): tree %.3g / %.3g, backtracked %.3g / %.3g" % (prec, mode, r0, o0, r1, o1))
 
 
+@pytest.mark.parametrize("prec", ["s", "d"])
+def test_no_representation_branch_takes_the_best_candidate(prec):
+    # test hook: every candidate child representation is turned down, so each
+    # cluster takes its best failed candidate (the smallest weighted growth)
+    # and is counted in reps_failed -- the branch of Algorithm 1, lines 15-17,
+    # for "no suitable representation".  On W_201 (clusters of two, whose
+    # candidates all have small growth) the results still meet the targets of
+    # the mixed mode and every eigenvalue matches the oracle.
+    import paper_1304_1864_gb300 as m
+    d, e = inputs.wilkinson(201)
+    d64, e64 = _acc.exact_input(d, e, prec)
+    W0, Z0, st0 = _solve(d, e, prec, "mixed")
+    W, Z, st = _solve(d, e, prec, "mixed", flags=m.MRRR_FLAG_TEST_NO_REP)
+    assert st0["reps_failed"] == 0 and st0["nclusters"] > 0
+    assert st["reps_failed"] >= st["nclusters"] > 0, (st["reps_failed"], st["nclusters"])
+    _acc.check_eigvals(d64, e64, W, prec, "mixed")
+    _acc.check_res_orth(d64, e64, W, Z, prec, "mixed")
+
+
 def test_rrr_test_reports_the_relative_condition():
     # with the relative-robustness test on, the n = 4001 Wilkinson matrix
     # (about 2000 clusters of two) reports the largest relative condition

@@ -134,3 +134,49 @@ def test_bad_requests_are_rejected_at_submit():
             srv.submit(d, e, W, Z, il=1, iu=9)
         with pytest.raises(m.MrrrError):
             srv.poll(12345, wait_ms=0)
+
+
+def test_cancel_withdraws_a_pending_request():
+    # one worker admitting one request at a time: while a larger request
+    # runs, the next one waits and can be withdrawn.  Its outputs stay as they
+    # were and its poll reports MRRR_ERR_CANCELLED; the running request
+    # completes as usual; a retired ticket cannot be cancelled; only completed
+    # requests are counted
+    import paper_1304_1864_gb300 as m
+    da, ea = inputs.make("121", 2001, seed=1)
+    db, eb = inputs.uniform_random(300, seed=2)
+    Wa = np.full(2001, np.nan, np.float32)
+    Za = np.full((2001, 2001), np.nan, np.float32)
+    Wb = np.full(300, np.nan, np.float32)
+    Zb = np.full((300, 300), np.nan, np.float32)
+    with m.Server(workers=1, max_batch=1) as srv:
+        ta = srv.submit(da.astype(np.float32), ea.astype(np.float32), Wa, Za)
+        tb = srv.submit(db.astype(np.float32), eb.astype(np.float32), Wb, Zb)
+        assert srv.cancel(tb) == m.MRRR_OK
+        rb, _ = srv.poll(tb)
+        ra, info = srv.poll(ta)
+        with pytest.raises(m.MrrrError):
+            srv.cancel(ta)
+        st = srv.stats()
+    assert rb == m.MRRR_ERR_CANCELLED and np.all(np.isnan(Wb)) and np.all(np.isnan(Zb))
+    assert ra == 0 and info["m"] == 2001 and st["completed"] == 1
+    d64, e64 = _acc.exact_input(da, ea, "s")
+    _acc.check_res_orth(d64, e64, Wa.astype(np.float64), Za.T, "s", "mixed")
+
+
+def test_out_of_memory_at_admission_fails_only_its_batch():
+    # test hook (alloc_failures): the first batch fails as if its device
+    # allocation had failed.  Its request completes with MRRR_ERR_NOMEM and
+    # its outputs untouched; the server goes on and serves the next requests
+    # as the same requests solved alone
+    import paper_1304_1864_gb300 as m
+    cases = [_make(*r, seed=51 + i) for i, r in enumerate(REQUESTS[1:4])]
+    with m.Server(workers=1, max_batch=1, alloc_failures=1) as srv:
+        tickets = [srv.submit(c[0][2], c[0][3], c[0][4], c[0][5], mode=r[3], il=r[4], iu=r[5])
+                   for r, c in zip(REQUESTS[1:4], cases)]
+        results = [srv.poll(t) for t in tickets]
+    assert results[0][0] == m.MRRR_ERR_NOMEM and results[0][1]["m"] == 0
+    assert np.all(np.isnan(_acc.as_np(cases[0][0][4])))
+    for (rc, info), (bufs, (W1, Z1)) in zip(results[1:], cases[1:]):
+        assert rc == 0
+        assert np.array_equal(_acc.as_np(bufs[4]), W1) and np.array_equal(_acc.as_np(bufs[5]).T, Z1)
