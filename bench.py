@@ -51,7 +51,7 @@ RQI_FLOPS = {"f64": (8.0, 3.0), "dd": (102.0, 22.0)}
 # DRAM bytes (read + write) per k_rqi launch on this workload, the mean over the
 # launches of one `ncu --set full` capture; valid only while the sources that
 # define the kernel hash to the value they had at the capture
-RQI_TRAFFIC = {"bytes_per_launch": 935.12e6, "sources_sha1": "b7b1b87401644a1c6d0f689fbdb2a3d2da4b49fb",
+RQI_TRAFFIC = {"bytes_per_launch": 935.12e6, "sources_sha1": "075ac0479d93b851d6f19eeec3cfdb9de873563b",
                "sources": ("mrrr_core.cuh", "mrrr_dd.cuh", "mrrr_fast.cuh", "mrrr_phases.cuh", "mrrr_solver.cuh",
                            "mrrr_types.cuh", "solver_s.cu")}
 

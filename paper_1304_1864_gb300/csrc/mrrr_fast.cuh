@@ -618,16 +618,19 @@ constexpr int kGp = 4;
 // v_r = 1 / R_{r+1}, v_{i+1} = -ld_i v_i.  The walk stores the multiplier of
 // z_i (P_{i-1} or R_{i+1}) in A[i]; the solve overwrites it with z_i.  A
 // vanished pivot needs no special rule here (z_{i+1} = 0 and z_i follow
-// from the neighbouring multipliers), and the underflowed tail of a
-// localized vector stays zero.
+// from the neighbouring multipliers), and entries of z below the normal
+// range (the tail of a localized vector) are zero.
 //
 // Where X leaves [2^-256, 2^256), X and Y are scaled by the power of two 2^k
 // that brings X into [1, 2) -- the ratios and the signs do not change --
 // right after X was stored, so that both the decision and k follow from the
-// stored value itself; the solve, reaching that entry, multiplies its
-// running factor by 2^k.  Both scalings work on the exponent fields
-// (dscale_bits), with no FP64 instruction.  An overflow, or a vanished pivot at the twist
-// (P_{r-1} or R_{r+1} zero), sends the step to the guarded generic solve.
+// stored value itself; the walk scales on the exponent fields (dscale_bits).
+// The solve keeps its running factor as a mantissa in [1, 2) and an integer
+// exponent, and reaching that entry adds k to the exponent.  Neither costs
+// an FP64 instruction, and the factor cannot underflow between two
+// far-apart peaks of the vector.  An overflow, or a vanished pivot at the
+// twist (P_{r-1} or R_{r+1} zero), sends the step to the guarded generic
+// solve.
 __device__ __forceinline__ TwistResult<double> twisted_fixed_proj(const double* __restrict__ rep, int n, double lam,
                                                                  double pivmin, double* __restrict__ A,
                                                                  double* __restrict__ B, double* gamma, int* imax,
