@@ -70,6 +70,15 @@ def glued_wilkinson(copies: int, block: int = 201, coupling: float = 1e-8):
     return d, e
 
 
+def glued_wilkinson_offset(copies: int, block: int, coupling: float, delta: float):
+    """glued_wilkinson with block c's diagonal raised by c * delta: the
+    matching eigenvalues of the copies stay close (a cluster) but apart from
+    one another, so no pair is degenerate to working precision, as the
+    symmetric gluing makes one."""
+    d, e = glued_wilkinson(copies, block, coupling)
+    return d + np.repeat(np.arange(copies) * delta, block), e
+
+
 def from_spectrum(lam, seed: int = 0):
     """A symmetric tridiagonal whose eigenvalues are ``lam``: the Lanczos
     tridiagonalisation of diag(lam) from a seeded random unit start vector

@@ -212,8 +212,7 @@ def test_backtracking_forced_by_the_test_hook(prec, mode, coupling, delta, gapto
     # 3.2, "The representation tree"); the results still meet the targets of
     # the mode and every eigenvalue matches the oracle.
     import paper_1304_1864_gb300 as m
-    d, e = inputs.glued_wilkinson(12, 21, coupling)
-    d = d + np.repeat(np.arange(12) * delta, 21)
+    d, e = inputs.glued_wilkinson_offset(12, 21, coupling, delta)
     d64, e64 = _acc.exact_input(d, e, prec)
     kw = {"gaptol": gaptol} if gaptol > 0 else {}
     W0, Z0, st0 = _solve(d, e, prec, mode, **kw)

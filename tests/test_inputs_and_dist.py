@@ -172,3 +172,32 @@ def test_partition_helpers():
         assert len(parts) == world and shard.check_parts(parts, n)
     assert not shard.check_parts([(1, 5), (7, 10)], 10)
     assert not shard.check_parts([(1, 5), (6, 9)], 10)
+
+
+@pytest.mark.parametrize("prec,coupling,delta", [("d", 1e-8, 1e-6), ("s", 1.5e-6, 1e-4)])
+def test_offset_glued_wilkinson_nests_clusters_without_a_degenerate_pair(prec, coupling, delta):
+    # the input of the backtracking test, from the oracle's eigenvalues: the
+    # top 24 eigenvalues lie within 1e-3 of one another relative to their
+    # size (one cluster at the root for gaptol 1e-3); they come in pairs much
+    # closer than the spread of the set (each pair a cluster again in the
+    # child made for the set) with the pairs well apart; and no two
+    # eigenvalues of the matrix agree to binary64 resolution.  The plain
+    # gluing of the same blocks has a pair that does.
+    import oracle
+
+    def eig(d, e):
+        if prec == "s":
+            d, e = d.astype(np.float32).astype(np.float64), e.astype(np.float32).astype(np.float64)
+        hi, lo = oracle.eigvals(d, e)
+        return hi, lo
+
+    hi, lo = eig(*inputs.glued_wilkinson_offset(12, 21, coupling, delta))
+    th, tl = hi[-24:], lo[-24:]
+    spread = (th[-1] - th[0]) + (tl[-1] - tl[0])
+    assert spread < 1e-3 * abs(th[0])
+    gaps = np.diff(th) + np.diff(tl)
+    assert np.all(gaps[0::2] < 1e-3 * spread / 4) and np.all(gaps[1::2] > 1e-3 * spread)
+    eps_d = 2.0 ** -53
+    assert (np.diff(hi) + np.diff(lo)).min() > 1e3 * eps_d * np.abs(hi).max()
+    h0, l0 = eig(*inputs.glued_wilkinson(12, 21, coupling))
+    assert (np.diff(h0) + np.diff(l0)).min() < eps_d * np.abs(h0).max()
